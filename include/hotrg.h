@@ -1,0 +1,182 @@
+/*
+ * hotrg.h -- C ABI of the GB300 HOTRG library (forward coarse-graining and
+ * its reverse-mode backward, "differentiable TRG").
+ *
+ * What is computed (paper: "Automatic Differentiation for Second
+ * Renormalization of Tensor Networks"):
+ *
+ *   - SM Sec. A: the partition function of a 2D lattice model is the trace
+ *     of a square network of identical rank-4 tensors T0[l][r][u][d].
+ *   - SM Sec. B, HOTRG step equation: one coarse-graining step merges two
+ *     vertically adjacent tensors,
+ *        T'[a][b][y][y'] = sum T[x1][x1'][y][j] T[x2][x2'][j][y']
+ *                              w[x1][x2][a] w[x1'][x2'][b],
+ *     with the isometry w taken from the local higher-order SVD of the
+ *     merged pair, i.e. the leading D' = min(X*X, d_cut) eigenvectors of the
+ *     Gram matrix G[(x1 x2)][(x1'' x2'')] of that pair (eigenvalues
+ *     descending; each eigenvector sign-fixed so that its largest-magnitude
+ *     component is positive).  Steps alternate direction (main text
+ *     Fig. 1a): before every step after the first the tensor is re-oriented
+ *     T[l][r][u][d] -> T[u][d][l][r].
+ *   - Normalisation: after step k the new tensor is divided by its
+ *     Frobenius norm c_k (computed in FP64).  With N = 2^n_steps sites,
+ *        ln Z / N = sum_k ln(c_k) / 2^k + ln|sum_{x,y} T_n[x][x][y][y]| / 2^n.
+ *   - Backward: SM Sec. B second-renormalization recursion = SM Sec. E
+ *     chain rule through the Jacobian of each step; main-text Eq. (1) for
+ *     the adjoint of w.  hotrg_backward returns d(ln Z / N)/d T0 (per site)
+ *     and, for Ising inputs, d(ln Z / N)/d beta.
+ *
+ * Layouts: every tensor is row-major T[l][r][u][d] (d fastest), float64.
+ *
+ * Ownership: the caller owns every buffer it passes.  A plan owns all device
+ * memory it needs (checkpoints, eigenvectors, workspaces); it is sized at
+ * hotrg_plan_create and nothing is allocated inside forward or backward.
+ *
+ * Threading: a plan is bound to one CUDA stream and is not thread-safe.
+ *
+ * Errors: every call returns a hotrg_status; no C++ exception crosses this
+ * boundary.  After any error the plan stays usable (a new forward must be run
+ * before a backward).  hotrg_last_error() gives a one-line description of the
+ * last error seen on a plan.
+ */
+#ifndef HOTRG_H
+#define HOTRG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  HOTRG_OK = 0,
+  HOTRG_EINVAL = 1,       /* bad argument (sizes, NULL, non-finite input)         */
+  HOTRG_ENOMEM = 2,       /* device allocation failed at plan creation             */
+  HOTRG_ECUDA = 3,        /* a CUDA runtime/driver/cuSOLVER call failed            */
+  HOTRG_ENOTCONV = 4,     /* the eigensolver reported non-convergence              */
+  HOTRG_ENONFINITE = 5,   /* a norm or the final trace was zero, NaN or infinite   */
+  HOTRG_ETIMEOUT = 6,     /* a bounded device-side wait gave up (error word set)   */
+  HOTRG_ESTATE = 7,       /* call out of order (backward before a forward)         */
+  HOTRG_EUNSUPPORTED = 8  /* option not available on this device or build          */
+} hotrg_status;
+
+typedef enum {
+  HOTRG_FP64 = 0,    /* every contraction in FP64 (CUDA cores)                         */
+  HOTRG_BF16X3 = 1,  /* contractions as split-BF16 tensor-core products: hi*hi + hi*lo
+                        + lo*hi, FP32 accumulation                                     */
+  HOTRG_BF16X6 = 2   /* three-plane split (hi, mid, lo): all products with plane-sum
+                        <= 2 (6 products), FP32 accumulation over K-chunks, chunks
+                        summed in compensated (double-float) precision                */
+} hotrg_precision;
+
+typedef struct {
+  int d0;               /* bond dimension of T0 (all four legs)                          */
+  int d_cut;            /* truncation: kept eigenvectors per step, D' = min(X*X, d_cut)   */
+  int n_steps;          /* number of coarse-graining steps (first one vertical)           */
+  int precision;        /* hotrg_precision for steps >= split_from_step                   */
+  int split_from_step;  /* 1-based; steps before it always run in FP64                   */
+  int want_grad;        /* 1: keep what hotrg_backward needs (eigenvectors per step)      */
+  int fixed_w_grad;     /* 1: backward holds every w fixed (SM Sec. E view of w as
+                           independent parameters); 0: full derivative through the eigh  */
+  double eigh_broadening; /* eta_rel in F = d / (d^2 + eta_rel * lam_1^2); <= 0 -> 1e-12 */
+} hotrg_config;
+
+typedef struct hotrg_plan_s* hotrg_plan;
+
+/* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
+ * fixed_w_grad = 0, eigh_broadening = 1e-12.  d0, d_cut, n_steps as given. */
+void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
+
+/* Device bytes a plan with this config would allocate (for admission control). */
+hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* cfg, size_t* bytes);
+
+/* Create a plan on the current CUDA device.  cuda_stream: a cudaStream_t
+ * (NULL = the legacy default stream).  All device memory is allocated here. */
+hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg_plan* out);
+void hotrg_plan_destroy(hotrg_plan plan);
+
+/* Forward from a caller tensor.  T0_host: d0^4 float64, host memory, layout
+ * [l][r][u][d].  Outputs (host, may be NULL): lnz_per_site (1 value),
+ * log_norms (n_steps values ln c_k), trace_sign (+1/-1 sign of the final
+ * trace).  Blocks until the results are on the host. */
+hotrg_status hotrg_forward_tensor(hotrg_plan plan, const double* T0_host,
+                                  double* lnz_per_site, double* log_norms, int* trace_sign);
+
+/* Forward for the square-lattice Ising model H = -J sum s_i s_j - h sum s_i
+ * (s = +-1), one tensor per spin, T0 built on the device from the Boltzmann
+ * weights (SM Sec. A): T0 = sum_s e^{beta h s} W[s][l] W[s][r] W[s][u] W[s][d],
+ * W[s][0] = sqrt(cosh beta J), W[s][1] = s sqrt(sinh beta J).  Needs
+ * beta*J >= 0 and d0 == 2.  Outputs as hotrg_forward_tensor. */
+hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double h,
+                                 double* lnz_per_site, double* log_norms, int* trace_sign);
+
+/* Device-resident forward: T0_dev is a device pointer (d0^4 float64); results
+ * are written to the device buffer out_dev = [lnz_per_site, trace_sign,
+ * ln c_1 .. ln c_n] (n_steps + 2 doubles).  Enqueued on the plan's stream;
+ * returns without synchronising.  Device-side failures (eigensolver,
+ * non-finite norm, timeouts) are reported by hotrg_sync. */
+hotrg_status hotrg_forward_device(hotrg_plan plan, const double* T0_dev, double* out_dev);
+
+/* Backward after a forward (needs want_grad = 1).  dlnz_dT0_host: d0^4
+ * float64 (host), d(ln Z / N)/d T0.  dlnz_dbeta_host: may be NULL; if not,
+ * the last forward must have been hotrg_forward_ising, and it receives
+ * d(ln Z / N)/d beta (the internal energy per site is its negative). */
+hotrg_status hotrg_backward(hotrg_plan plan, double* dlnz_dT0_host, double* dlnz_dbeta_host);
+
+/* Device-resident backward: writes d(ln Z/N)/d T0 (d0^4 float64) to grad_dev. */
+hotrg_status hotrg_backward_device(hotrg_plan plan, double* grad_dev);
+
+/* Wait for the plan's stream and report any device-side failure. */
+hotrg_status hotrg_sync(hotrg_plan plan);
+
+/* Per-step diagnostics of the last forward (host arrays of n_steps, may be
+ * NULL): trunc_err = sum of discarded eigenvalues / sum of all; cut_gap =
+ * (lam_D' - lam_D'+1) / lam_1 (0 where nothing is cut); step_is_split = 1
+ * where the step ran in the split tensor-core precision. */
+hotrg_status hotrg_diagnostics(hotrg_plan plan, double* trunc_err, double* cut_gap,
+                               int* step_is_split);
+
+/* Per-step bond dimensions of a plan: X (merged legs), Y (other legs), X' (kept). */
+hotrg_status hotrg_step_dims(hotrg_plan plan, int step, int* X, int* Y, int* Xp);
+
+const char* hotrg_status_string(hotrg_status s);
+const char* hotrg_last_error(hotrg_plan plan);
+
+/* Device capability check: HOTRG_OK if the current device can run the split
+ * tensor-core path (compute capability 10.3). */
+hotrg_status hotrg_device_supports_split(void);
+
+/* Per-stage timing.  hotrg_profile_enable(plan, 1) creates a pool of CUDA
+ * events (outside any forward/backward) and from then on brackets every stage
+ * launch with events on the plan's stream; 0 turns it off.
+ * hotrg_profile_read synchronises the stream and returns, per slot, the summed
+ * milliseconds and the number of bracketed launches since the last read (both
+ * arrays hold HOTRG_PROFILE_SLOTS entries; counts may be NULL), then resets.
+ * Slots: 0 Gram, 1 eigensolve (+ sort/sign fix), 2 stage-1 contraction,
+ * 3 stage-2 contraction (the O(D^7) GEMM), 4 stage-3 contraction, 5 norm,
+ * 6 operand preparation (bf16 split), 7 backward contractions, 8 backward
+ * eigensolve adjoint, 9 backward Gram adjoint; slot + 16 = the same stage run
+ * by the FP64 GEMM instead of the tensor-core GEMM. */
+#define HOTRG_PROFILE_SLOTS 32
+hotrg_status hotrg_profile_enable(hotrg_plan plan, int enable);
+hotrg_status hotrg_profile_read(hotrg_plan plan, double* ms, int* counts);
+
+/* Number of kernels this library has launched in this process (all plans). */
+unsigned long long hotrg_kernel_launches(void);
+
+/* Kernel checks (used by the test-suite; not part of the HOTRG path).
+ * C = A B^T for row-major float64 host matrices A (M x K), B (N x K), C (M x N),
+ * computed on the device by the split-BF16 tensor-core GEMM (planes = 2 or 3
+ * bf16 planes per operand, FP32 accumulation in chunks of kchunk * 64 along K,
+ * 0 = a single chunk; K must be a multiple of 8) or by the FP64 GEMM.  They
+ * allocate and free temporary device memory and synchronise the device. */
+hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
+                                    const double* B, double* C);
+hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const double* B, double* C);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HOTRG_H */

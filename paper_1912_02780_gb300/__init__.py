@@ -1,0 +1,261 @@
+"""GB300 HOTRG: forward coarse-graining and reverse-mode backward of
+differentiable TRG, as a thin Python binding over the C ABI in
+``include/hotrg.h`` (argument marshalling only; every step runs in the CUDA
+library ``_lib/libhotrg.so``).
+
+The library must be built first (``__graft_entry__.build()`` or
+``python paper_1912_02780_gb300/_build.py``).  There is no CPU fallback: if
+the library is missing, loading fails with an error.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libhotrg.so")
+
+FP64, BF16X3, BF16X6 = 0, 1, 2
+PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "bf16x6": BF16X6}
+
+STATUS = {0: "HOTRG_OK", 1: "HOTRG_EINVAL", 2: "HOTRG_ENOMEM", 3: "HOTRG_ECUDA",
+          4: "HOTRG_ENOTCONV", 5: "HOTRG_ENONFINITE", 6: "HOTRG_ETIMEOUT",
+          7: "HOTRG_ESTATE", 8: "HOTRG_EUNSUPPORTED"}
+
+# Every symbol declared in include/hotrg.h.
+EXPORTS = (
+    "hotrg_config_default", "hotrg_plan_workspace_bytes", "hotrg_plan_create",
+    "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
+    "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
+    "hotrg_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
+    "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
+    "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
+)
+PROFILE_SLOTS = 32
+STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
+               7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj"}
+
+
+class hotrg_config(ctypes.Structure):
+    _fields_ = [("d0", ctypes.c_int), ("d_cut", ctypes.c_int), ("n_steps", ctypes.c_int),
+                ("precision", ctypes.c_int), ("split_from_step", ctypes.c_int),
+                ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
+                ("eigh_broadening", ctypes.c_double)]
+
+
+class HotrgError(RuntimeError):
+    def __init__(self, status: int, msg: str = ""):
+        self.status = status
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+
+
+_LIB = None
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int)
+
+
+def lib() -> ctypes.CDLL:
+    """Load the CUDA library (raises if it was not built)."""
+    global _LIB
+    if _LIB is not None:
+        return _LIB
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"HOTRG CUDA library not built: {LIB_PATH} is missing "
+                           "(run __graft_entry__.build())")
+    L = ctypes.CDLL(LIB_PATH)
+    vp = ctypes.c_void_p
+    L.hotrg_config_default.argtypes = [ctypes.POINTER(hotrg_config), ctypes.c_int, ctypes.c_int, ctypes.c_int]
+    L.hotrg_config_default.restype = None
+    L.hotrg_plan_workspace_bytes.argtypes = [ctypes.POINTER(hotrg_config), ctypes.POINTER(ctypes.c_size_t)]
+    L.hotrg_plan_create.argtypes = [ctypes.POINTER(hotrg_config), vp, ctypes.POINTER(vp)]
+    L.hotrg_plan_destroy.argtypes = [vp]
+    L.hotrg_plan_destroy.restype = None
+    L.hotrg_forward_tensor.argtypes = [vp, _dp, _dp, _dp, _ip]
+    L.hotrg_forward_ising.argtypes = [vp, ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _dp, _ip]
+    L.hotrg_forward_device.argtypes = [vp, vp, vp]
+    L.hotrg_backward.argtypes = [vp, _dp, _dp]
+    L.hotrg_backward_device.argtypes = [vp, vp]
+    L.hotrg_sync.argtypes = [vp]
+    L.hotrg_diagnostics.argtypes = [vp, _dp, _dp, _ip]
+    L.hotrg_step_dims.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip]
+    L.hotrg_status_string.argtypes = [ctypes.c_int]
+    L.hotrg_status_string.restype = ctypes.c_char_p
+    L.hotrg_last_error.argtypes = [vp]
+    L.hotrg_last_error.restype = ctypes.c_char_p
+    L.hotrg_device_supports_split.argtypes = []
+    L.hotrg_gemm_split_check.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp]
+    L.hotrg_gemm_f64_check.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp]
+    L.hotrg_profile_enable.argtypes = [vp, ctypes.c_int]
+    L.hotrg_profile_read.argtypes = [vp, _dp, _ip]
+    L.hotrg_kernel_launches.argtypes = []
+    L.hotrg_kernel_launches.restype = ctypes.c_ulonglong
+    for name in EXPORTS:
+        if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
+                        "hotrg_last_error", "hotrg_kernel_launches"):
+            getattr(L, name).restype = ctypes.c_int
+    _LIB = L
+    return L
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(_dp)
+
+
+def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_step: int = 1,
+                want_grad: bool = True, fixed_w_grad: bool = False,
+                eigh_broadening: float = 1e-12) -> hotrg_config:
+    c = hotrg_config()
+    lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
+    c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+    c.split_from_step = split_from_step
+    c.want_grad = int(bool(want_grad))
+    c.fixed_w_grad = int(bool(fixed_w_grad))
+    c.eigh_broadening = eigh_broadening
+    return c
+
+
+def workspace_bytes(d0, d_cut, n_steps, **kw) -> int:
+    c = make_config(d0, d_cut, n_steps, **kw)
+    out = ctypes.c_size_t(0)
+    s = lib().hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out))
+    if s:
+        raise HotrgError(s, "workspace size")
+    return out.value
+
+
+def device_supports_split() -> bool:
+    return lib().hotrg_device_supports_split() == 0
+
+
+class Plan:
+    """One HOTRG problem shape (d0, d_cut, n_steps, precision) bound to a
+    CUDA stream; owns all device memory it needs."""
+
+    def __init__(self, d0: int, d_cut: int, n_steps: int, precision="fp64",
+                 split_from_step: int = 1, want_grad: bool = True, fixed_w_grad: bool = False,
+                 eigh_broadening: float = 1e-12, stream: Optional[int] = None):
+        self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
+                               fixed_w_grad, eigh_broadening)
+        self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
+        h = ctypes.c_void_p(0)
+        s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if s:
+            raise HotrgError(s, "hotrg_plan_create")
+        self._h = h
+
+    def _check(self, s, what):
+        if s:
+            msg = lib().hotrg_last_error(self._h)
+            raise HotrgError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def forward_tensor(self, T0: np.ndarray):
+        T0 = np.ascontiguousarray(T0, dtype=np.float64)
+        if T0.shape != (self.d0,) * 4:
+            raise ValueError("T0 must have shape (d0, d0, d0, d0)")
+        lnz = ctypes.c_double(0)
+        ln = np.zeros(self.n_steps)
+        sign = ctypes.c_int(0)
+        self._check(lib().hotrg_forward_tensor(self._h, _p(T0), ctypes.byref(lnz), _p(ln),
+                                               ctypes.byref(sign)), "forward_tensor")
+        return lnz.value, ln, sign.value
+
+    def forward_ising(self, beta: float, J: float = 1.0, h: float = 0.0):
+        lnz = ctypes.c_double(0)
+        ln = np.zeros(self.n_steps)
+        sign = ctypes.c_int(0)
+        self._check(lib().hotrg_forward_ising(self._h, beta, J, h, ctypes.byref(lnz), _p(ln),
+                                              ctypes.byref(sign)), "forward_ising")
+        return lnz.value, ln, sign.value
+
+    def forward_device(self, T0_ptr: int, out_ptr: int):
+        self._check(lib().hotrg_forward_device(self._h, ctypes.c_void_p(T0_ptr),
+                                               ctypes.c_void_p(out_ptr)), "forward_device")
+
+    def backward(self, want_dbeta: bool = False):
+        g = np.zeros((self.d0,) * 4)
+        db = ctypes.c_double(0)
+        self._check(lib().hotrg_backward(self._h, _p(g), ctypes.byref(db) if want_dbeta else None),
+                    "backward")
+        return (g, db.value) if want_dbeta else g
+
+    def backward_device(self, grad_ptr: int):
+        self._check(lib().hotrg_backward_device(self._h, ctypes.c_void_p(grad_ptr)), "backward_device")
+
+    def sync(self):
+        self._check(lib().hotrg_sync(self._h), "sync")
+
+    def diagnostics(self):
+        t = np.zeros(self.n_steps)
+        g = np.zeros(self.n_steps)
+        s = np.zeros(self.n_steps, dtype=np.int32)
+        self._check(lib().hotrg_diagnostics(self._h, _p(t), _p(g), s.ctypes.data_as(_ip)), "diagnostics")
+        return t, g, s
+
+    def step_dims(self, k: int):
+        X, Y, Xp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(lib().hotrg_step_dims(self._h, k, ctypes.byref(X), ctypes.byref(Y), ctypes.byref(Xp)),
+                    "step_dims")
+        return X.value, Y.value, Xp.value
+
+    def profile(self, enable: bool = True):
+        self._check(lib().hotrg_profile_enable(self._h, int(bool(enable))), "profile_enable")
+
+    def profile_read(self):
+        """{slot name: (ms, launches)}; FP64-GEMM variants get the suffix _f64."""
+        ms = np.zeros(PROFILE_SLOTS)
+        cnt = np.zeros(PROFILE_SLOTS, dtype=np.int32)
+        self._check(lib().hotrg_profile_read(self._h, _p(ms), cnt.ctypes.data_as(_ip)), "profile_read")
+        out = {}
+        for i in range(PROFILE_SLOTS):
+            if cnt[i]:
+                name = STAGE_NAMES.get(i % 16, str(i % 16)) + ("_f64" if i >= 16 else "")
+                out[name] = (float(ms[i]), int(cnt[i]))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().hotrg_plan_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def kernel_launches() -> int:
+    return int(lib().hotrg_kernel_launches())
+
+
+def gemm_split_check(A: np.ndarray, B: np.ndarray, planes: int = 2, kchunk: int = 0) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N))
+    s = lib().hotrg_gemm_split_check(M, N, K, planes, kchunk, _p(A), _p(B), _p(C))
+    if s:
+        raise HotrgError(s, "gemm_split_check")
+    return C
+
+
+def gemm_f64_check(A: np.ndarray, B: np.ndarray) -> np.ndarray:
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    B = np.ascontiguousarray(B, dtype=np.float64)
+    M, K = A.shape
+    N = B.shape[0]
+    C = np.zeros((M, N))
+    s = lib().hotrg_gemm_f64_check(M, N, K, _p(A), _p(B), _p(C))
+    if s:
+        raise HotrgError(s, "gemm_f64_check")
+    return C

@@ -1,0 +1,557 @@
+// Split-BF16 GEMM on the sm_103a tensor cores (tcgen05 + TMEM + TMA).
+//
+//   C(m, n) = alpha * sum_k A(m, k) * B(n, k)
+//
+// Both operands are K-major and split into bf16 planes (hi, lo [, lo2]) so
+// that a*b ~= sum over the plane pairs (i, j) with i + j <= nplanes - 1 of
+// a_i * b_j.  This is how the O(D^7) contractions of the HOTRG step (SM
+// Sec. B, HOTRG step equation) and of its adjoint run at tensor-core rate
+// while keeping about 16 (two planes) or 24 (three planes) significant bits
+// per product.
+//
+// Structure (one persistent CTA per SM, 192 threads):
+//   warp 4      TMA producer: per 64-wide K slab, one 3-D tensor-map load per
+//               operand plane into a 128B-swizzled shared-memory stage.
+//   warp 5      MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16)
+//               for every plane pair and K step; tcgen05.commit frees the
+//               stage and, at the end of an accumulation chunk, hands the
+//               TMEM accumulator (double-buffered) to the epilogue.
+//   warps 0-3   epilogue: tcgen05.ld the accumulator (one TMEM lane per row),
+//               optionally add the chunk into a compensated float-float sum kept
+//               in TMEM, and write the tile through the output index maps as
+//               FP32, FP64 or split bf16 planes.
+// Every mbarrier wait is bounded; on timeout the error word gets kErrTimeout,
+// the role stops, and all warps still meet at the final barrier, drain their
+// MMAs and free TMEM.
+#include <cuda.h>
+#include <cstdio>
+#include <mutex>
+#include "gemm_tc.h"
+
+namespace hotrg {
+
+namespace {
+
+constexpr int BM = 128;
+constexpr int BK = 64;                       // 64 bf16 = 128 bytes = one swizzle row
+constexpr long long kTimeoutCycles = 4000000000LL;   // about 2 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait: true when the phase with this parity completed, false (and
+// the error word set) after about two seconds.
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+  if (mbar_try_wait(bar, parity)) return true;
+  long long t0 = clock64();
+  while (true) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (clock64() - t0 > kTimeoutCycles) {
+      atomicOr(err, kErrTimeout);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm, uint32_t bar,
+                                            int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)tm), "r"(bar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                   bar)
+               : "memory");
+}
+__device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                       uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+  uint32_t r[16];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+      "{%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, %16};" ::"r"(taddr),
+      "r"(__float_as_uint(v[0])), "r"(__float_as_uint(v[1])), "r"(__float_as_uint(v[2])),
+      "r"(__float_as_uint(v[3])), "r"(__float_as_uint(v[4])), "r"(__float_as_uint(v[5])),
+      "r"(__float_as_uint(v[6])), "r"(__float_as_uint(v[7])), "r"(__float_as_uint(v[8])),
+      "r"(__float_as_uint(v[9])), "r"(__float_as_uint(v[10])), "r"(__float_as_uint(v[11])),
+      "r"(__float_as_uint(v[12])), "r"(__float_as_uint(v[13])), "r"(__float_as_uint(v[14])),
+      "r"(__float_as_uint(v[15]))
+      : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld_wait() {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_st_wait() {
+  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor for a K-major tile written by TMA with
+// 128-byte swizzle: rows of 128 bytes, 8-row groups 1024 bytes apart (SBO),
+// descriptor version 1, layout SWIZZLE_128B (= 2 in bits 61-63).  Advancing
+// along K inside the 128-byte row is done by adding the byte offset to the
+// start address (the swizzle is a function of the absolute address; tiles are
+// 1024-byte aligned).
+__device__ __forceinline__ uint64_t sdesc_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for this layout)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // swizzle 128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+         ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void named_bar(int id, int count) {
+  asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int BN, int NP>
+struct Cfg {
+  static constexpr int kAPlane = BM * BK * 2;
+  static constexpr int kBPlane = BN * BK * 2;
+  static constexpr int kStage = NP * (kAPlane + kBPlane);
+  static constexpr int kStages = (200 * 1024 / kStage) > 4 ? 4 : (200 * 1024 / kStage);
+  static constexpr int kBars = 2 * kStages + 5;
+  static constexpr int kSmem = 1024 + kStages * kStage + kBars * 8 + BN * 8 + BN / 16 * 4 + 16;
+  static constexpr int kTmemCols = (4 * BN <= 512) ? 4 * BN : 2 * BN;
+  static_assert(kStages >= 2, "need at least two pipeline stages");
+};
+
+// 16 consecutive output columns of one row.  When their offsets are
+// contiguous and aligned (flag `contig`, precomputed per tile) the row segment
+// is written with 16-byte vector stores, otherwise element by element.
+template <int BN, int NP>
+__device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff,
+                                                 const long long* cn_s, int contig, int cc,
+                                                 const float* hi, const float* lo) {
+  const long long off0 = coff + cn_s[cc];
+  if (contig && off0 >= 0 && off0 + 15 < p.c_lim && !p.accumulate) {
+    if (p.out_mode == kOutSplit && (off0 & 7) == 0) {
+      __nv_bfloat16 b[3][16];
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        float h = p.alpha * hi[j], l = p.alpha * lo[j];
+        b[0][j] = __float2bfloat16_rn(h);
+        float r = (h - __bfloat162float(b[0][j])) + l;
+        b[1][j] = __float2bfloat16_rn(r);
+        b[2][j] = __float2bfloat16_rn(r - __bfloat162float(b[1][j]));
+      }
+      __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(p.C) + off0;
+#pragma unroll
+      for (int q = 0; q < 3; ++q) {
+        if (q >= p.out_planes) break;
+        uint4* d = reinterpret_cast<uint4*>(c + q * p.out_plane_stride);
+        d[0] = *reinterpret_cast<const uint4*>(&b[q][0]);
+        d[1] = *reinterpret_cast<const uint4*>(&b[q][8]);
+      }
+      return;
+    }
+    if (p.out_mode == kOutF32 && (off0 & 3) == 0) {
+      float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(p.C) + off0);
+#pragma unroll
+      for (int q = 0; q < 4; ++q)
+        d[q] = make_float4(p.alpha * (hi[4 * q] + lo[4 * q]), p.alpha * (hi[4 * q + 1] + lo[4 * q + 1]),
+                           p.alpha * (hi[4 * q + 2] + lo[4 * q + 2]),
+                           p.alpha * (hi[4 * q + 3] + lo[4 * q + 3]));
+      return;
+    }
+    if (p.out_mode == kOutF64 && (off0 & 1) == 0) {
+      double2* d = reinterpret_cast<double2*>(reinterpret_cast<double*>(p.C) + off0);
+#pragma unroll
+      for (int q = 0; q < 8; ++q)
+        d[q] = make_double2((double)p.alpha * ((double)hi[2 * q] + (double)lo[2 * q]),
+                            (double)p.alpha * ((double)hi[2 * q + 1] + (double)lo[2 * q + 1]));
+      return;
+    }
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    long long co = cn_s[cc + j];
+    if (co < 0) continue;
+    long long off = coff + co;
+    if (off >= p.c_lim) {
+      atomicOr(p.err, kErrBounds);
+      continue;
+    }
+    if (p.out_mode == kOutF32) {
+      float v = p.alpha * (hi[j] + lo[j]);
+      float* c = reinterpret_cast<float*>(p.C) + off;
+      if (p.accumulate) v += *c;
+      *c = v;
+    } else if (p.out_mode == kOutF64) {
+      double v = (double)p.alpha * ((double)hi[j] + (double)lo[j]);
+      double* c = reinterpret_cast<double*>(p.C) + off;
+      if (p.accumulate) v += *c;
+      *c = v;
+    } else {
+      __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(p.C) + off;
+      float h = p.alpha * hi[j], l = p.alpha * lo[j];
+      __nv_bfloat16 b0 = __float2bfloat16_rn(h);
+      float r = (h - __bfloat162float(b0)) + l;
+      c[0] = b0;
+      if (p.out_planes > 1) {
+        __nv_bfloat16 b1 = __float2bfloat16_rn(r);
+        c[p.out_plane_stride] = b1;
+        if (p.out_planes > 2) c[2 * p.out_plane_stride] = __float2bfloat16_rn(r - __bfloat162float(b1));
+      }
+    }
+  }
+}
+
+template <int BN, int NP>
+__global__ void __launch_bounds__(192, 1)
+    tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
+                   const TcGemm p) {
+  using C = Cfg<BN, NP>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
+                                             ~static_cast<uintptr_t>(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
+  long long* cn_s = reinterpret_cast<long long*>(bars + C::kBars);
+  int* cv_s = reinterpret_cast<int*>(cn_s + BN);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cv_s + BN / 16);
+
+  const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const uint32_t bar0 = smem_u32(bars);
+  auto full_bar = [&](int s) { return bar0 + 8u * s; };
+  auto empty_bar = [&](int s) { return bar0 + 8u * (C::kStages + s); };
+  auto tfull_bar = [&](int a) { return bar0 + 8u * (2 * C::kStages + a); };
+  auto tempty_bar = [&](int a) { return bar0 + 8u * (2 * C::kStages + 2 + a); };
+  const uint32_t drain_bar = bar0 + 8u * (2 * C::kStages + 4);
+  const uint32_t smem0 = smem_u32(smem);
+  auto a_tile = [&](int s, int pl) { return smem0 + s * C::kStage + pl * C::kAPlane; };
+  auto b_tile = [&](int s, int pl) {
+    return smem0 + s * C::kStage + NP * C::kAPlane + pl * C::kBPlane;
+  };
+
+  if (warp == 4 && lane == 0) {
+    for (int s = 0; s < C::kStages; ++s) {
+      mbar_init(full_bar(s), 1);
+      mbar_init(empty_bar(s), 1);
+    }
+    for (int a = 0; a < 2; ++a) {
+      mbar_init(tfull_bar(a), 1);
+      mbar_init(tempty_bar(a), 4);
+    }
+    mbar_init(drain_bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
+  }
+  if (warp == 5) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                     smem_u32(tmem_slot)),
+                 "r"(C::kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  const int MT = (p.M + BM - 1) / BM, NT = (p.N + BN - 1) / BN;
+  const long long tiles = (long long)MT * NT;
+  const int KB = (p.K + BK - 1) / BK;
+  const int kchunk = p.kchunk < 1 ? KB : (p.kchunk > KB ? KB : p.kchunk);
+  const int nchunks = (KB + kchunk - 1) / kchunk;
+  const bool compensated = (nchunks > 1) && (4 * BN <= 512);
+
+  if (warp == 4) {
+    if (lane == 0) {
+      int s = 0;
+      uint32_t ph = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        const int mt = (int)(t / NT), nt = (int)(t % NT);
+        for (int kb = 0; kb < KB; ++kb) {
+          if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err)) { ok = false; break; }
+          mbar_expect_tx(full_bar(s), C::kStage);
+#pragma unroll
+          for (int pl = 0; pl < NP; ++pl)
+            tma_load_3d(a_tile(s, pl), &tmA, full_bar(s), kb * BK, mt * BM, pl);
+#pragma unroll
+          for (int pl = 0; pl < NP; ++pl)
+            tma_load_3d(b_tile(s, pl), &tmB, full_bar(s), kb * BK, nt * BN, pl);
+          if (++s == C::kStages) { s = 0; ph ^= 1u; }
+        }
+      }
+      if (!ok) {
+        // Let copies already in flight land before the CTA can exit.
+        for (int s2 = 0; s2 < C::kStages; ++s2) mbar_wait(full_bar(s2), 0, p.err);
+      }
+    }
+  } else if (warp == 5) {
+    if (lane == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int s = 0;
+      uint32_t ph = 0;
+      int acc = 0;
+      uint32_t acc_ph = 0;
+      bool ok = true;
+      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+        for (int c = 0; c < nchunks && ok; ++c) {
+          if (!mbar_wait(tempty_bar(acc), acc_ph ^ 1u, p.err)) { ok = false; break; }
+          tc_fence_after();
+          const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+          const int kb0 = c * kchunk, kb1 = min(KB, kb0 + kchunk);
+          for (int kb = kb0; kb < kb1; ++kb) {
+            if (!mbar_wait(full_bar(s), ph, p.err)) { ok = false; break; }
+            tc_fence_after();
+            for (int q = 0; q < p.npairs; ++q) {
+              const uint32_t a0 = a_tile(s, p.pa[q]), b0 = b_tile(s, p.pb[q]);
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk) {
+                tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
+                       (kb > kb0 || q > 0 || kk > 0) ? 1u : 0u);
+              }
+            }
+            tc_commit(empty_bar(s));
+            if (++s == C::kStages) { s = 0; ph ^= 1u; }
+          }
+          if (!ok) break;
+          tc_commit(tfull_bar(acc));
+          if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+        }
+      }
+      // All MMAs issued by this thread must finish before TMEM is freed.
+      tc_commit(drain_bar);
+      mbar_wait(drain_bar, 0, p.err);
+    }
+  } else {
+    // Epilogue warps 0..3: warp w owns TMEM lanes [32w, 32w + 32) = tile rows.
+    int acc = 0;
+    uint32_t acc_ph = 0;
+    bool ok = true;
+    const int row = warp * 32 + lane;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(warp * 32) << 16);
+    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      const int mt = (int)(t / NT), nt = (int)(t % NT);
+      const int m0 = mt * BM, n0 = nt * BN;
+      named_bar(1, 128);
+      for (int j = threadIdx.x; j < BN; j += 128)
+        cn_s[j] = (n0 + j < p.N) ? imap(p.cn, n0 + j) : -1;
+      named_bar(1, 128);
+      if (threadIdx.x < BN / 16) {
+        int ok = cn_s[threadIdx.x * 16] >= 0;
+        for (int j = 1; j < 16 && ok; ++j)
+          ok = (cn_s[threadIdx.x * 16 + j] == cn_s[threadIdx.x * 16 + j - 1] + 1);
+        cv_s[threadIdx.x] = ok;
+      }
+      named_bar(1, 128);
+      const int m = m0 + row;
+      const bool mok = m < p.M;
+      const long long coff = mok ? imap(p.cm, m) : 0;
+      for (int c = 0; c < nchunks; ++c) {
+        if (!mbar_wait(tfull_bar(acc), acc_ph, p.err)) { ok = false; break; }
+        tc_fence_after();
+        const uint32_t tacc = lane_base + (uint32_t)(acc * BN);
+        const uint32_t thi = lane_base + (uint32_t)(2 * BN), tlo = thi + BN;
+        const bool last = (c == nchunks - 1);
+        for (int cc = 0; cc < BN; cc += 16) {
+          float v[16], hi[16], lo[16];
+          tmem_ld16(tacc + cc, v);
+          if (compensated && c > 0) {
+            tmem_ld16(thi + cc, hi);
+            tmem_ld16(tlo + cc, lo);
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+              float s, e;
+              two_sum(hi[j], v[j], s, e);
+              e += lo[j];
+              hi[j] = s + e;
+              lo[j] = e - (hi[j] - s);
+            }
+          } else {
+            tmem_ld_wait();
+#pragma unroll
+            for (int j = 0; j < 16; ++j) { hi[j] = v[j]; lo[j] = 0.f; }
+          }
+          if (compensated && !last) {
+            tmem_st16(thi + cc, hi);
+            tmem_st16(tlo + cc, lo);
+          } else if (last && mok) {
+            store_tile_chunk<BN, NP>(p, coff, cn_s, cv_s[cc / 16], cc, hi, lo);
+          }
+        }
+        if (compensated && !last) tmem_st_wait();
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
+      }
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  if (warp == 5) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                 "r"(C::kTmemCols)
+                 : "memory");
+  }
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn get_encode() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(f);
+  });
+  return fn;
+}
+
+bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows) {
+  EncodeTiledFn enc = get_encode();
+  if (!enc) return false;
+  cuuint64_t dims[3] = {(cuuint64_t)op.K, (cuuint64_t)op.rows, (cuuint64_t)op.planes};
+  cuuint64_t strides[2] = {(cuuint64_t)op.K * 2, (cuuint64_t)op.plane_stride * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, 1};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = enc(tm, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<__nv_bfloat16*>(op.ptr), dims,
+                   strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+template <int BN, int NP>
+cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,
+                   int num_sms) {
+  using C = Cfg<BN, NP>;
+  CUtensorMap ta, tb;
+  if (!make_map(&ta, A, BM) || !make_map(&tb, B, BN)) return cudaErrorInvalidValue;
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  long long tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
+  int grid = (int)(tiles < num_sms ? tiles : num_sms);
+  count_launch();
+  tc_gemm_kernel<BN, NP><<<grid, 192, C::kSmem, stream>>>(ta, tb, g);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+void tc_set_pairs(TcGemm& g, int nplanes) {
+  g.nplanes = nplanes;
+  if (nplanes == 2) {
+    const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+    g.npairs = 3;
+    for (int i = 0; i < 3; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
+  } else {
+    // smallest products first, the hi*hi product last
+    const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+    g.npairs = 6;
+    for (int i = 0; i < 6; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
+  }
+}
+
+cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,
+                    int num_sms) {
+  if (g.M <= 0 || g.N <= 0) return cudaSuccess;
+  if (A.K != B.K || A.K != g.K || A.K % 8 != 0 || A.rows < g.M || B.rows < g.N ||
+      A.planes != g.nplanes || B.planes != g.nplanes)
+    return cudaErrorInvalidValue;
+  if ((reinterpret_cast<uintptr_t>(A.ptr) | reinterpret_cast<uintptr_t>(B.ptr)) & 15)
+    return cudaErrorInvalidValue;
+  const bool comp = g.kchunk > 0 && g.kchunk < (g.K + BK - 1) / BK;
+  if (g.nplanes == 2) {
+    if (!comp && g.N > 128) return launch<256, 2>(A, B, g, stream, num_sms);
+    if (g.N > 64) return launch<128, 2>(A, B, g, stream, num_sms);
+    return launch<64, 2>(A, B, g, stream, num_sms);
+  }
+  if (g.nplanes == 3) {
+    if (g.N > 64) return launch<128, 3>(A, B, g, stream, num_sms);
+    return launch<64, 3>(A, B, g, stream, num_sms);
+  }
+  return cudaErrorInvalidValue;
+}
+
+}  // namespace hotrg

@@ -1,0 +1,43 @@
+// Split-BF16 tcgen05 GEMM (see gemm_tc.cu).
+#pragma once
+#include "common.cuh"
+
+namespace hotrg {
+
+// A K-major operand stored as `planes` bf16 planes [plane][rows][K] (K a
+// multiple of 8 so that every row starts on a 16-byte boundary).
+struct TcOperand {
+  const __nv_bfloat16* ptr;
+  int rows, K, planes;
+  long long plane_stride;   // elements between planes (>= rows * K)
+};
+
+enum TcOutMode : int { kOutF32 = 0, kOutF64 = 1, kOutSplit = 2 };
+
+struct TcGemm {
+  int M, N, K;
+  int nplanes;               // operand planes (2 or 3)
+  int npairs;                // products formed per K slab
+  int pa[6], pb[6];          // plane of A / of B for each product
+  int kchunk;                // K-blocks (of 64) per FP32 accumulation chunk; chunks are summed
+                             // in compensated float-float; >= ceil(K/64) means one chunk
+  IMap cm, cn;               // output element (m, n) at C + cm(m) + cn(n)
+  int out_mode;              // TcOutMode
+  int out_planes;            // planes written for kOutSplit
+  long long out_plane_stride;
+  void* C;
+  float alpha;               // output = alpha * sum
+  int accumulate;            // kOutF32/kOutF64: C += output
+  long long c_lim;           // elements per output plane: stores at or beyond are skipped
+                             // and flagged (kErrBounds)
+  int* err;                  // device error word
+};
+
+// Set the products of a precision: nplanes = 2 -> {hh, hl, lh};
+// nplanes = 3 -> {hh, hm, mh, hl, mm, lh}.
+void tc_set_pairs(TcGemm& g, int nplanes);
+
+cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,
+                    int num_sms);
+
+}  // namespace hotrg

@@ -1,0 +1,1023 @@
+// Plan / executor and C ABI of the HOTRG library (declared in include/hotrg.h).
+//
+// A plan fixes the bond-dimension schedule of every step, allocates all device
+// memory once, and runs each coarse-graining step as a short sequence of
+// kernels on one CUDA stream:
+//
+//   Gram (SM Sec. B: isometry from the local HOSVD of the merged pair)
+//     A = T.T over (x1', y), B = T.T over (x2', y'), G = sum_{j j'} A B
+//   FP64 eigensolve of G (cuSOLVER), descending order, sign fix
+//   HOTRG step equation (SM Sec. B) as three GEMMs, chunked over the free leg y
+//     S1: U[(y x1' a)][(x2 j)]   = sum_{x1} T[x1 x1' y j] w[x1 x2 a]
+//     S2: V[(y a y')][(x1' x2')] = sum_{x2 j} U T[x2 x2' j y']
+//     S3: T'[y][y'][a][b]        = sum_{x1' x2'} V w[x1' x2' b]
+//     (written directly in the re-oriented layout used by the next step)
+//   FP64 Frobenius normalisation and log-norm.
+//
+// Steps marked "split" run the Gram and S1-S3 on the tcgen05 split-BF16 GEMM;
+// the others (and the whole FP64 precision mode) use the FP64 GEMM.  The
+// backward (SM Sec. B recursion = SM Sec. E chain rule, main-text Eq. (1) for
+// the adjoint of w, plus the adjoint of the truncated eigensolve and of the
+// Gram assembly) recomputes U and V per step from the stored T_k and w_k.
+#include <cusolverDn.h>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/hotrg.h"
+#include "common.cuh"
+#include "gemm_f64.h"
+#include "gemm_tc.h"
+#include "kernels.h"
+
+using namespace hotrg;
+
+namespace {
+
+constexpr long long kChunkF64 = 1LL << 27;     // FP64 stage chunk budget (elements)
+constexpr long long kChunkSplit = 1LL << 30;   // split stage chunk budget (elements per plane)
+constexpr int kMaxPartial = 4096;
+
+struct StepGeom {
+  int X, Y, Xp;
+  long long N;        // X * X
+  bool split;
+  int yc64, ycs;      // y-chunk of the FP64 and split stage buffers
+};
+
+long long round_up(long long v, long long m) { return (v + m - 1) / m * m; }
+
+struct Layout {
+  std::vector<StepGeom> g;
+  long long maxT = 0, maxN = 0, maxN2 = 0, maxXp = 0;
+  long long chunk64 = 0, chunkS = 0;       // elements
+  long long splitT = 0, splitG = 0, splitW1 = 0, splitW3 = 0;   // elements per plane
+  long long totalE = 0, totalT = 0, totalLam = 0;
+  int np = 0;
+  bool any_split = false;
+};
+
+int planes_of(int precision) {
+  return precision == HOTRG_BF16X6 ? 3 : (precision == HOTRG_BF16X3 ? 2 : 0);
+}
+
+bool build_layout(const hotrg_config& c, Layout& L) {
+  L = Layout();
+  L.np = planes_of(c.precision);
+  long long X = c.d0, Y = c.d0;
+  for (int k = 1; k <= c.n_steps; ++k) {
+    StepGeom s;
+    s.X = (int)X;
+    s.Y = (int)Y;
+    s.N = X * X;
+    long long Xp = s.N < c.d_cut ? s.N : c.d_cut;
+    s.Xp = (int)Xp;
+    s.split = L.np > 0 && k >= c.split_from_step && X % 8 == 0 && Y % 8 == 0 && Xp % 8 == 0;
+    long long per_y = X * X * Xp * Y;
+    long long a = kChunkF64 / per_y;
+    s.yc64 = (int)(a < 1 ? 1 : (a > Y ? Y : a));
+    long long b = kChunkSplit / per_y;
+    s.ycs = (int)(b < 1 ? 1 : (b > Y ? Y : b));
+    if (s.N > (1LL << 31) / 2 || X * X * Y * Y > (1LL << 31) || per_y * Y > (1LL << 42)) return false;
+    L.g.push_back(s);
+    long long tin = X * X * Y * Y, tout = Y * Y * Xp * Xp;
+    if (tin > L.maxT) L.maxT = tin;
+    if (tout > L.maxT) L.maxT = tout;
+    if (s.N > L.maxN) L.maxN = s.N;
+    if (s.N * s.N > L.maxN2) L.maxN2 = s.N * s.N;
+    if (Xp > L.maxXp) L.maxXp = Xp;
+    L.totalT += tout;
+    L.totalE += c.want_grad ? s.N * s.N : 0;
+    L.totalLam += s.N;
+    long long c64 = (long long)s.yc64 * per_y;
+    if (c64 > L.chunk64) L.chunk64 = c64;
+    if (s.split) {
+      L.any_split = true;
+      long long cs = (long long)s.ycs * per_y;
+      if (cs > L.chunkS) L.chunkS = cs;
+      if (tin > L.splitT) L.splitT = tin;
+      if (X * X * Y * Y > L.splitG) L.splitG = X * X * Y * Y;
+      if (Xp * X * X > L.splitW1) L.splitW1 = Xp * X * X;
+      if (Xp * X * X > L.splitW3) L.splitW3 = Xp * X * X;
+    }
+    Y = Xp;           // T' is (Xp, Xp, Y, Y), stored re-oriented as (Y, Y, Xp, Xp)
+    X = s.Y;
+  }
+  L.totalT += (long long)c.d0 * c.d0 * c.d0 * c.d0;
+  L.chunkS = round_up(L.chunkS, 64);
+  L.splitT = round_up(L.splitT, 64);
+  L.splitG = round_up(L.splitG, 64);
+  L.splitW1 = round_up(L.splitW1, 64);
+  L.splitW3 = round_up(L.splitW3, 64);
+  return true;
+}
+
+struct Bytes {
+  size_t total = 0;
+  void add(long long elems, size_t elsize) { total += round_up(elems * (long long)elsize, 256); }
+};
+
+}  // namespace
+
+struct hotrg_plan_s {
+  hotrg_config cfg;
+  Layout L;
+  cudaStream_t stream = nullptr;
+  cusolverDnHandle_t solver = nullptr;
+  int sms = 152;
+  std::vector<void*> allocs;
+  std::vector<size_t> alloc_bytes;
+  std::vector<double*> T, E, lam;
+  double *Escr = nullptr, *wasc = nullptr, *work = nullptr;
+  int lwork = 0;
+  int* info = nullptr;
+  double *Abuf = nullptr, *Bbuf = nullptr, *Abar = nullptr, *Bbar = nullptr;
+  double *Ub = nullptr, *Vb = nullptr, *Pb = nullptr, *Qb = nullptr;
+  double *Sb = nullptr, *Hb = nullptr, *wbT = nullptr, *Gb = nullptr;
+  double *Ecur = nullptr, *Enext = nullptr, *Tbar = nullptr;
+  double *dT0 = nullptr, *partial = nullptr, *scal = nullptr, *log_norms = nullptr, *out = nullptr;
+  double *dtrunc = nullptr, *dgap = nullptr;
+  int* err = nullptr;
+  __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
+                *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
+  bool have_fwd = false, fwd_ising = false;
+  std::string last_error;
+  // optional per-stage CUDA-event timing
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_pool;
+  size_t ev_used = 0;
+  std::vector<std::pair<int, size_t>> prof_rec;
+};
+
+namespace {
+
+std::atomic<unsigned long long> g_launches{0};
+
+// Brackets one stage of the path with CUDA events on the plan's stream when
+// profiling is on (slot = stage id, + 16 for the FP64 variant of a contraction).
+struct Stage {
+  hotrg_plan p;
+  int slot;
+  size_t idx;
+  Stage(hotrg_plan p_, int slot_) : p(p_), slot(slot_), idx((size_t)-1) {
+    if (p->prof && p->ev_used + 2 <= p->ev_pool.size()) {
+      idx = p->ev_used;
+      p->ev_used += 2;
+      cudaEventRecord(p->ev_pool[idx], p->stream);
+    }
+  }
+  ~Stage() {
+    if (idx != (size_t)-1) {
+      cudaEventRecord(p->ev_pool[idx + 1], p->stream);
+      p->prof_rec.push_back({slot, idx});
+    }
+  }
+};
+
+hotrg_status fail(hotrg_plan p, hotrg_status s, const std::string& msg) {
+  if (p) p->last_error = msg;
+  return s;
+}
+
+#define CK(call)                                                                   \
+  do {                                                                             \
+    cudaError_t e_ = (call);                                                       \
+    if (e_ != cudaSuccess)                                                         \
+      return fail(p, HOTRG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename T>
+hotrg_status dalloc(hotrg_plan p, T** ptr, long long elems) {
+  *ptr = nullptr;
+  if (elems <= 0) return HOTRG_OK;
+  void* v = nullptr;
+  if (cudaMalloc(&v, (size_t)elems * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return fail(p, HOTRG_ENOMEM, "cudaMalloc failed");
+  }
+  p->allocs.push_back(v);
+  p->alloc_bytes.push_back((size_t)elems * sizeof(T));
+  *ptr = reinterpret_cast<T*>(v);
+  return HOTRG_OK;
+}
+
+// Elements of size `elsize` from ptr to the end of the plan allocation that
+// holds it (0 if none does): the bound every kernel access is checked against.
+long long lim_of(const hotrg_plan p, const void* ptr, size_t elsize) {
+  const char* c = reinterpret_cast<const char*>(ptr);
+  for (size_t i = 0; i < p->allocs.size(); ++i) {
+    const char* b = reinterpret_cast<const char*>(p->allocs[i]);
+    if (c >= b && c < b + p->alloc_bytes[i]) return (long long)((b + p->alloc_bytes[i] - c) / elsize);
+  }
+  return 0;
+}
+
+#define AL(ptr, n)                                \
+  do {                                            \
+    hotrg_status s_ = dalloc(p, &(ptr), (n));     \
+    if (s_ != HOTRG_OK) return s_;                \
+  } while (0)
+
+hotrg_status validate(const hotrg_config* c) {
+  if (!c) return HOTRG_EINVAL;
+  if (c->d0 < 1 || c->d_cut < 1 || c->n_steps < 1 || c->n_steps > 200) return HOTRG_EINVAL;
+  if (c->precision < HOTRG_FP64 || c->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
+  if (c->split_from_step < 1) return HOTRG_EINVAL;
+  return HOTRG_OK;
+}
+
+GemmF64 g64(const hotrg_plan p, const double* A, IMap am, IMap ak, const double* B, IMap bn,
+            IMap bk, double* C, IMap cm, IMap cn, int M, int N, int K, double alpha, double beta) {
+  GemmF64 g;
+  g.a_lim = lim_of(p, A, sizeof(double));
+  g.b_lim = lim_of(p, B, sizeof(double));
+  g.c_lim = lim_of(p, C, sizeof(double));
+  g.err = p->err;
+  g.A = A; g.am = am; g.ak = ak;
+  g.B = B; g.bn = bn; g.bk = bk;
+  g.C = C; g.cm = cm; g.cn = cn;
+  g.M = M; g.N = N; g.K = K;
+  g.alpha = alpha; g.beta = beta;
+  g.a_kfast = (ak.s0 == 1) ? 1 : 0;
+  g.b_kfast = (bk.s0 == 1) ? 1 : 0;
+  return g;
+}
+
+TcGemm tcg(const hotrg_plan p, int M, int N, int K, IMap cm, IMap cn, int mode, void* C,
+           long long out_plane_stride) {
+  TcGemm g;
+  memset(&g, 0, sizeof(g));
+  tc_set_pairs(g, p->L.np);
+  g.M = M; g.N = N; g.K = K;
+  g.kchunk = (p->L.np == 3) ? 1 : 4;
+  g.cm = cm; g.cn = cn;
+  g.out_mode = mode;
+  g.out_planes = p->L.np;
+  g.out_plane_stride = out_plane_stride;
+  g.C = C;
+  g.alpha = 1.f;
+  g.accumulate = 0;
+  g.c_lim = lim_of(p, C, mode == kOutF64 ? 8 : (mode == kOutF32 ? 4 : 2));
+  if (mode == kOutSplit && out_plane_stride > 0 && g.c_lim > out_plane_stride)
+    g.c_lim = out_plane_stride;
+  g.err = p->err;
+  return g;
+}
+
+cudaError_t gsplit(const hotrg_plan p, const double* src, IMap rm, IMap km, int rows, int K,
+                   int np, long long stride, __nv_bfloat16* dst) {
+  return gather_split(src, lim_of(p, src, sizeof(double)), rm, km, rows, K, np, stride, dst, p->err,
+                      p->stream, p->sms);
+}
+
+TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long stride) {
+  TcOperand o;
+  o.ptr = ptr; o.rows = rows; o.K = K; o.planes = planes; o.plane_stride = stride;
+  return o;
+}
+
+// ---- forward pieces -------------------------------------------------------
+
+enum StageId { kStGram = 0, kStEigh = 1, kStS1 = 2, kStS2 = 3, kStS3 = 4, kStNorm = 5,
+               kStPrep = 6, kStBwdContract = 7, kStBwdEigh = 8, kStBwdGram = 9, kStF64 = 16 };
+
+hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* A, double* B,
+                      double* G) {
+  Stage sc(p, kStGram + kStF64);
+  const int X = s.X, Y = s.Y;
+  const long long XY2 = (long long)X * Y * Y, Y2 = (long long)Y * Y;
+  cudaStream_t st = p->stream;
+  CK(gemm_f64(g64(p, T, map2(Y, 1, XY2), map2(Y, Y, Y2), T, map2(Y, 1, XY2), map2(Y, Y, Y2), A,
+                  map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y, 1.0, 0.0),
+              st, p->sms));
+  CK(gemm_f64(g64(p, T, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, Y, XY2), map2(Y, 1, Y2), B,
+                  map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y, 1.0, 0.0),
+              st, p->sms));
+  if (G)
+    CK(gemm_f64(g64(p, A, map_lin(Y2), map_lin(1), B, map_lin(Y2), map_lin(1), G,
+                    map2(X, X, (long long)X * X * X), map2(X, 1, (long long)X * X), X * X, X * X,
+                    Y * Y, 1.0, 0.0),
+                st, p->sms));
+  return HOTRG_OK;
+}
+
+hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double* G) {
+  const int X = s.X, Y = s.Y, np = p->L.np;
+  const long long XY2 = (long long)X * Y * Y, Y2 = (long long)Y * Y;
+  cudaStream_t st = p->stream;
+  const long long sT = p->L.splitT, sG = p->L.splitG;
+  {
+    Stage sc(p, kStPrep);
+    CK(gsplit(p, T, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, np, sT, p->pTA));
+    CK(gsplit(p, T, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, np, sT, p->pTB));
+  }
+  Stage sc(p, kStGram);
+  TcOperand ta = opnd(p->pTA, X * Y, X * Y, np, sT), tb = opnd(p->pTB, X * Y, X * Y, np, sT);
+  CK(tc_gemm(ta, ta, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutSplit, p->pA, sG),
+             st, p->sms));
+  CK(tc_gemm(tb, tb, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutSplit, p->pB, sG),
+             st, p->sms));
+  TcOperand a = opnd(p->pA, X * X, Y * Y, np, sG), b = opnd(p->pB, X * X, Y * Y, np, sG);
+  CK(tc_gemm(a, b, tcg(p, X * X, X * X, Y * Y, map2(X, X, (long long)X * X * X),
+                       map2(X, 1, (long long)X * X), kOutF64, G, 0),
+             st, p->sms));
+  return HOTRG_OK;
+}
+
+hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, const double* Ek,
+                          double* Tout) {
+  const int X = s.X, Y = s.Y, Xp = s.Xp;
+  const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
+  const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X;
+  cudaStream_t st = p->stream;
+  for (int y0 = 0; y0 < Y; y0 += s.yc64) {
+    const int yc = (Y - y0) < s.yc64 ? (Y - y0) : s.yc64;
+    {
+      Stage sc(p, kStS1 + kStF64);
+      CK(gemm_f64(g64(p, Ek, map2(X, 1, N), map_lin(X), T + (long long)y0 * Y, map3(Y, X, 1, Y2, Y),
+                      map_lin(XY2), p->Ub, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
+                      Xp * X, yc * X * Y, X, 1.0, 0.0),
+                  st, p->sms));
+    }
+    {
+      Stage sc(p, kStS2 + kStF64);
+      CK(gemm_f64(g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
+                      map3(Xp, X, Y * X2, X, Xp * Y * X2), map2(X, 1, X2), yc * X * Xp, Y * X,
+                      X * Y, 1.0, 0.0),
+                  st, p->sms));
+    }
+    {
+      Stage sc(p, kStS3 + kStF64);
+      CK(gemm_f64(g64(p, p->Vb, map_lin(X2), map_lin(1), Ek, map_lin(N), map_lin(1),
+                      Tout + (long long)y0 * Y * Xp2, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1),
+                      yc * Xp * Y, Xp, X * X, 1.0, 0.0),
+                  st, p->sms));
+    }
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, const double* Ek,
+                            double* Tout) {
+  const int X = s.X, Y = s.Y, Xp = s.Xp, np = p->L.np;
+  const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
+  const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X;
+  cudaStream_t st = p->stream;
+  const long long sT = p->L.splitT, sW1 = p->L.splitW1, sW3 = p->L.splitW3, sC = p->L.chunkS;
+  // operands shared by all y-chunks
+  {
+  Stage sc(p, kStPrep);
+  CK(gsplit(p, Ek, map2(X, 1, N), map_lin(X), Xp * X, X, np, sW1, p->pW1));
+  CK(gsplit(p, T, map3(Y, X, 1, Y2, Y), map_lin(XY2), Y * X * Y, X, np, sT, p->pT1));
+  CK(gsplit(p, T, map2(X, Y2, 1), map2(Y, Y, XY2), Y * X, X * Y, np, sT, p->pP));
+  CK(gsplit(p, Ek, map_lin(N), map_lin(1), Xp, X * X, np, sW3, p->pW3));
+  }
+  const TcOperand w1 = opnd(p->pW1, Xp * X, X, np, sW1);
+  const TcOperand pp = opnd(p->pP, Y * X, X * Y, np, sT);
+  const TcOperand w3 = opnd(p->pW3, Xp, X * X, np, sW3);
+  for (int y0 = 0; y0 < Y; y0 += s.ycs) {
+    const int yc = (Y - y0) < s.ycs ? (Y - y0) : s.ycs;
+    const TcOperand t1 = opnd(p->pT1 + (long long)y0 * X * Y * X, yc * X * Y, X, np, sT);
+    {
+    Stage sc(p, kStS1);
+    CK(tc_gemm(w1, t1,
+               tcg(p, Xp * X, yc * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
+                   kOutSplit, p->pU, sC),
+               st, p->sms));
+    }
+    const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
+    {
+    Stage sc(p, kStS2);
+    CK(tc_gemm(u, pp,
+               tcg(p, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
+                   map2(X, 1, X2), kOutSplit, p->pV, sC),
+               st, p->sms));
+    }
+    const TcOperand v = opnd(p->pV, yc * Xp * Y, X * X, np, sC);
+    Stage sc(p, kStS3);
+    CK(tc_gemm(v, w3,
+               tcg(p, yc * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1), kOutF64,
+                   Tout + (long long)y0 * Y * Xp2, 0),
+               st, p->sms));
+  }
+  return HOTRG_OK;
+}
+
+double* E_of(hotrg_plan p, int k) { return p->cfg.want_grad ? p->E[k - 1] : p->E[0]; }
+
+hotrg_status step_forward(hotrg_plan p, int k) {
+  const StepGeom& s = p->L.g[k - 1];
+  cudaStream_t st = p->stream;
+  const double* T = p->T[k - 1];
+  double* Tout = p->T[k];
+  double* Ek = E_of(p, k);
+  double* lk = p->lam[k - 1];
+  const int N = (int)s.N;
+  hotrg_status r;
+  if (s.split) r = gram_split(p, s, T, p->Escr);
+  else r = gram_f64(p, s, T, p->Abuf, p->Bbuf, p->Escr);
+  if (r != HOTRG_OK) return r;
+  {
+  Stage sc(p, kStEigh);
+  cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                         CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc, p->work,
+                                         p->lwork, p->info);
+  if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
+  CK(eigh_info_check(p->info, p->err, st));
+  CK(eig_desc(p->Escr, p->wasc, N, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
+  CK(eig_diag(lk, N, s.Xp, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
+  }
+  if (s.split) r = contract_split(p, s, T, Ek, Tout);
+  else r = contract_f64(p, s, T, Ek, Tout);
+  if (r != HOTRG_OK) return r;
+  const long long n_out = (long long)s.Y * s.Y * s.Xp * s.Xp;
+  Stage sc(p, kStNorm);
+  CK(frob_normalize(Tout, n_out, p->partial, kMaxPartial, p->log_norms + (k - 1), p->scal, p->err,
+                    st, p->sms));
+  return HOTRG_OK;
+}
+
+hotrg_status run_forward(hotrg_plan p) {
+  cudaStream_t st = p->stream;
+  for (int k = 1; k <= p->cfg.n_steps; ++k) {
+    hotrg_status r = step_forward(p, k);
+    if (r != HOTRG_OK) return r;
+  }
+  const StepGeom& last = p->L.g.back();
+  CK(trace_lnz(p->T[p->cfg.n_steps], last.Y, last.Xp, p->log_norms, p->cfg.n_steps, p->out,
+               p->scal + 1, p->err, st));
+  return HOTRG_OK;
+}
+
+// ---- backward pieces ------------------------------------------------------
+
+hotrg_status step_backward_f64(hotrg_plan p, int k) {
+  const StepGeom& s = p->L.g[k - 1];
+  const int X = s.X, Y = s.Y, Xp = s.Xp;
+  const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
+  const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X, YXp2 = (long long)Y * Xp2;
+  cudaStream_t st = p->stream;
+  const double* T = p->T[k - 1];
+  const double* Ek = E_of(p, k);
+  const double* lk = p->lam[k - 1];
+  double* Eb = p->Ecur;                    // 2^k dL/dT~_k, stored layout [y][y'][a][b]
+  CK(scale_exp_neg(Eb, Y2 * Xp2, p->log_norms + (k - 1), st, p->sms));   // -> dL/dT' (x 2^k)
+  CK(cudaMemsetAsync(p->Tbar, 0, sizeof(double) * X2 * Y2, st));
+  CK(cudaMemsetAsync(p->wbT, 0, sizeof(double) * Xp * N, st));
+  {
+  Stage sc(p, kStBwdContract + kStF64);
+  for (int y0 = 0; y0 < Y; y0 += s.yc64) {
+    const int yc = (Y - y0) < s.yc64 ? (Y - y0) : s.yc64;
+    const double* Ty = T + (long long)y0 * Y;
+    const double* Eby = Eb + (long long)y0 * YXp2;
+    // recompute U and V of this chunk (as in the forward)
+    CK(gemm_f64(g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
+                    map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY), Xp * X, yc * X * Y, X,
+                    1.0, 0.0),
+                st, p->sms));
+    CK(gemm_f64(g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
+                    map3(Xp, X, Y * X2, X, Xp * Y * X2), map2(X, 1, X2), yc * X * Xp, Y * X,
+                    X * Y, 1.0, 0.0),
+                st, p->sms));
+    // P[(y a i)][(k z)] = sum_b Tbar'[a b y z] w[i k b]
+    CK(gemm_f64(g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
+                    p->Pb, map3(Y, Xp, 1, X2 * Y, (long long)Xp * X2 * Y), map2(X, Y, XY),
+                    yc * Xp * Y, X * X, Xp, 1.0, 0.0),
+                st, p->sms));
+    // Q[(y a i)][(b j)] = sum_{k z} P T[b k j z]
+    CK(gemm_f64(g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
+                    map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0),
+                st, p->sms));
+    // upper copy: Tbar[a i y j] += sum_{A b} w[a b A] Q[y A i b j]
+    CK(gemm_f64(g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
+                    map2(X, Y, X * XY), p->Tbar + (long long)y0 * Y, map_lin(XY2),
+                    map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0),
+                st, p->sms));
+    // lower copy: Tbar[b k j z] += sum_{y i A} U[y i A b j] P[y A z i k]
+    CK(gemm_f64(g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
+                    map2(Y, 1, Y), map3(Xp, X, X * XY, XY, (long long)Xp * X * XY), p->Tbar,
+                    map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0),
+                st, p->sms));
+    // w carrying alpha: wbT[A][(a b)] += sum_{y i j} T[a i y j] Q[y A i b j]
+    CK(gemm_f64(g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
+                    map3(Y, X, 1, XY, (long long)Xp * X * XY), p->wbT, map_lin(X), map2(X, 1, N),
+                    X, Xp * X, yc * X * Y, 1.0, 1.0),
+                st, p->sms));
+    // w carrying beta: wbT[B][(i k)] += sum_{y A z} V[y A z][(i k)] Tbar'[A B y z]
+    CK(gemm_f64(g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
+                    map_lin(1), map3(Y, Xp, Xp2, Xp, YXp2), p->wbT, map_lin(1), map_lin(N),
+                    X * X, Xp, yc * Xp * Y, 1.0, 1.0),
+                st, p->sms));
+  }
+  }
+  if (!p->cfg.fixed_w_grad && Xp < N) {
+    Stage sc(p, kStBwdEigh + kStF64);
+    const int nd = (int)(N - Xp);
+    const double* Ud = Ek + (long long)Xp * N;
+    // S[j][k] = sum_i U_d[i][j] wbar[i][k]
+    CK(gemm_f64(g64(p, Ud, map_lin(N), map_lin(1), p->wbT, map_lin(N), map_lin(1), p->Sb,
+                    map_lin(Xp), map_lin(1), nd, Xp, (int)N, 1.0, 0.0),
+                st, p->sms));
+    double eta = p->cfg.eigh_broadening > 0 ? p->cfg.eigh_broadening : 1e-12;
+    CK(eigh_adj_scale(p->Sb, nd, Xp, lk, eta, st, p->sms));
+    // H[i][k] = sum_j U_d[i][j] FS[j][k];  Gbar[i][i'] = sum_k H[i][k] U_k[i'][k]
+    CK(gemm_f64(g64(p, Ud, map_lin(1), map_lin(N), p->Sb, map_lin(1), map_lin(Xp), p->Hb,
+                    map_lin(Xp), map_lin(1), (int)N, Xp, nd, 1.0, 0.0),
+                st, p->sms));
+    CK(gemm_f64(g64(p, p->Hb, map_lin(Xp), map_lin(1), Ek, map_lin(1), map_lin(N), p->Gb,
+                    map_lin(N), map_lin(1), (int)N, (int)N, Xp, 1.0, 0.0),
+                st, p->sms));
+    CK(symmetrize(p->Gb, (int)N, st, p->sms));
+    hotrg_status r = gram_f64(p, s, T, p->Abuf, p->Bbuf, nullptr);
+    if (r != HOTRG_OK) return r;
+    const long long X3 = X2 * X;
+    // Abar[(x1 x1'')][(j j')] = sum_{x2 x2''} Gbar[x1 x2 x1'' x2''] B[(x2 x2'')][(j j')]
+    CK(gemm_f64(g64(p, p->Gb, map2(X, X, X3), map2(X, 1, X2), p->Bbuf, map_lin(1), map_lin(Y2),
+                    p->Abar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0),
+                st, p->sms));
+    CK(gemm_f64(g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
+                    p->Bbar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0),
+                st, p->sms));
+    // Tbar[a i y j] += 2 sum_{c k} Abar[a j c k] T[c i y k]
+    CK(gemm_f64(g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
+                    map2(Y, 1, XY2), p->Tbar, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, X * Y,
+                    2.0, 1.0),
+                st, p->sms));
+    // Tbar[b k j z] += 2 sum_{d m} Bbar[b j d m] T[d k m z]
+    CK(gemm_f64(g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
+                    map2(Y, Y, XY2), p->Tbar, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y,
+                    2.0, 1.0),
+                st, p->sms));
+  }
+  // E_{k-1} = (1/2) Tbar (average of the two copies), in the layout of T_{k-1}
+  CK(scale_copy(p->Tbar, p->Enext, X2 * Y2, 0.5, st, p->sms));
+  double* tmp = p->Ecur;
+  p->Ecur = p->Enext;
+  p->Enext = tmp;
+  return HOTRG_OK;
+}
+
+hotrg_status run_backward(hotrg_plan p) {
+  const StepGeom& last = p->L.g.back();
+  CK(seed_trace_adjoint(p->Ecur, last.Y, last.Xp, p->scal + 1, p->stream, p->sms));
+  for (int k = p->cfg.n_steps; k >= 1; --k) {
+    hotrg_status r = step_backward_f64(p, k);
+    if (r != HOTRG_OK) return r;
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status check_device_error(hotrg_plan p) {
+  int e = 0;
+  CK(cudaMemcpy(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e & kErrTimeout) return fail(p, HOTRG_ETIMEOUT, "device wait timed out");
+  if (e & kErrEigh) return fail(p, HOTRG_ENOTCONV, "eigensolver did not converge");
+  if (e & kErrNonFinite) return fail(p, HOTRG_ENONFINITE, "norm or trace not finite");
+  if (e & kErrBounds) return fail(p, HOTRG_ECUDA, "a kernel index check failed (access skipped)");
+  if (e) return fail(p, HOTRG_ECUDA, "device error word set");
+  return HOTRG_OK;
+}
+
+hotrg_status finish_sync(hotrg_plan p) {
+  CK(cudaStreamSynchronize(p->stream));
+  return check_device_error(p);
+}
+
+}  // namespace
+
+namespace hotrg {
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+}  // namespace hotrg
+
+extern "C" {
+
+unsigned long long hotrg_kernel_launches(void) { return g_launches.load(); }
+
+hotrg_status hotrg_profile_enable(hotrg_plan p, int enable) {
+  if (!p) return HOTRG_EINVAL;
+  if (enable && p->ev_pool.empty()) {
+    p->ev_pool.resize(8192);
+    for (auto& e : p->ev_pool)
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        e = nullptr;
+        return fail(p, HOTRG_ECUDA, "cudaEventCreate failed");
+      }
+  }
+  p->prof = enable != 0;
+  p->ev_used = 0;
+  p->prof_rec.clear();
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_profile_read(hotrg_plan p, double* ms, int* counts) {
+  if (!p || !ms) return HOTRG_EINVAL;
+  CK(cudaStreamSynchronize(p->stream));
+  for (int i = 0; i < HOTRG_PROFILE_SLOTS; ++i) {
+    ms[i] = 0.0;
+    if (counts) counts[i] = 0;
+  }
+  for (const auto& r : p->prof_rec) {
+    float t = 0.f;
+    if (cudaEventElapsedTime(&t, p->ev_pool[r.second], p->ev_pool[r.second + 1]) == cudaSuccess) {
+      ms[r.first] += t;
+      if (counts) counts[r.first] += 1;
+    }
+  }
+  p->ev_used = 0;
+  p->prof_rec.clear();
+  return HOTRG_OK;
+}
+
+void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
+  if (!c) return;
+  memset(c, 0, sizeof(*c));
+  c->d0 = d0;
+  c->d_cut = d_cut;
+  c->n_steps = n_steps;
+  c->precision = HOTRG_FP64;
+  c->split_from_step = 1;
+  c->want_grad = 1;
+  c->fixed_w_grad = 0;
+  c->eigh_broadening = 1e-12;
+}
+
+hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
+  if (validate(c) != HOTRG_OK || !bytes) return HOTRG_EINVAL;
+  Layout L;
+  if (!build_layout(*c, L)) return HOTRG_EINVAL;
+  Bytes b;
+  b.add(L.totalT, 8);
+  b.add(c->want_grad ? L.totalE : L.maxN2, 8);
+  b.add(L.totalLam, 8);
+  b.add(L.maxN2, 8);          // Escr
+  b.add(L.maxN, 8);           // wasc
+  b.add(L.maxT, 8 * 4);       // Abuf Bbuf Abar Bbar
+  b.add(L.chunk64, 8 * 2);    // Ub Vb
+  if (c->want_grad) {
+    b.add(L.chunk64, 8 * 2);  // Pb Qb
+    b.add(L.maxN * L.maxXp, 8 * 3);
+    b.add(L.maxN2, 8);
+    b.add(L.maxT, 8 * 3);
+  }
+  if (L.any_split) {
+    b.add(L.splitT * L.np, 2 * 4);
+    b.add(L.splitG * L.np, 2 * 2);
+    b.add((L.splitW1 + L.splitW3) * L.np, 2);
+    b.add(L.chunkS * L.np, 2 * 2);
+  }
+  b.total += (size_t)64 << 20;  // solver workspace and small buffers (estimate)
+  *bytes = b.total;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg_plan* out) {
+  if (!out) return HOTRG_EINVAL;
+  *out = nullptr;
+  if (validate(cfg) != HOTRG_OK) return HOTRG_EINVAL;
+  hotrg_plan p = new hotrg_plan_s();
+  p->cfg = *cfg;
+  if (!build_layout(*cfg, p->L)) {
+    delete p;
+    return HOTRG_EINVAL;
+  }
+  p->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  auto cleanup = [&](hotrg_status s) {
+    hotrg_plan_destroy(p);
+    return s;
+  };
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return cleanup(HOTRG_ECUDA);
+  cudaDeviceProp prop;
+  if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return cleanup(HOTRG_ECUDA);
+  p->sms = prop.multiProcessorCount;
+  if (p->L.any_split && !(prop.major == 10 && prop.minor == 3)) return cleanup(HOTRG_EUNSUPPORTED);
+  const Layout& L = p->L;
+  const int n = cfg->n_steps;
+  hotrg_status s;
+#define ALC(ptr, cnt)                          \
+  do {                                         \
+    s = dalloc(p, &(ptr), (cnt));              \
+    if (s != HOTRG_OK) return cleanup(s);      \
+  } while (0)
+  p->T.resize(n + 1);
+  ALC(p->T[0], (long long)cfg->d0 * cfg->d0 * cfg->d0 * cfg->d0);
+  for (int k = 1; k <= n; ++k) {
+    const StepGeom& g = L.g[k - 1];
+    ALC(p->T[k], (long long)g.Y * g.Y * g.Xp * g.Xp);
+  }
+  if (cfg->want_grad) {
+    p->E.resize(n);
+    for (int k = 1; k <= n; ++k) ALC(p->E[k - 1], L.g[k - 1].N * L.g[k - 1].N);
+  } else {
+    p->E.resize(1);
+    ALC(p->E[0], L.maxN2);
+  }
+  p->lam.resize(n);
+  for (int k = 1; k <= n; ++k) ALC(p->lam[k - 1], L.g[k - 1].N);
+  ALC(p->Escr, L.maxN2);
+  ALC(p->wasc, L.maxN);
+  ALC(p->Abuf, L.maxT);
+  ALC(p->Bbuf, L.maxT);
+  ALC(p->Ub, L.chunk64);
+  ALC(p->Vb, L.chunk64);
+  if (cfg->want_grad) {
+    ALC(p->Pb, L.chunk64);
+    ALC(p->Qb, L.chunk64);
+    ALC(p->Abar, L.maxT);
+    ALC(p->Bbar, L.maxT);
+    ALC(p->Sb, L.maxN * L.maxXp);
+    ALC(p->Hb, L.maxN * L.maxXp);
+    ALC(p->wbT, L.maxN * L.maxXp);
+    ALC(p->Gb, L.maxN2);
+    ALC(p->Ecur, L.maxT);
+    ALC(p->Enext, L.maxT);
+    ALC(p->Tbar, L.maxT);
+  }
+  ALC(p->dT0, 64);
+  ALC(p->partial, kMaxPartial);
+  ALC(p->scal, 8);
+  ALC(p->log_norms, n);
+  ALC(p->out, n + 2);
+  ALC(p->dtrunc, n);
+  ALC(p->dgap, n);
+  ALC(p->err, 4);
+  ALC(p->info, 4);
+  if (L.any_split) {
+    const int np = L.np;
+    ALC(p->pTA, L.splitT * np);
+    ALC(p->pTB, L.splitT * np);
+    ALC(p->pT1, L.splitT * np);
+    ALC(p->pP, L.splitT * np);
+    ALC(p->pA, L.splitG * np);
+    ALC(p->pB, L.splitG * np);
+    ALC(p->pW1, L.splitW1 * np);
+    ALC(p->pW3, L.splitW3 * np);
+    ALC(p->pU, L.chunkS * np);
+    ALC(p->pV, L.chunkS * np);
+  }
+  if (cusolverDnCreate(&p->solver) != CUSOLVER_STATUS_SUCCESS) return cleanup(HOTRG_ECUDA);
+  if (cusolverDnSetStream(p->solver, p->stream) != CUSOLVER_STATUS_SUCCESS)
+    return cleanup(HOTRG_ECUDA);
+  int lw = 0;
+  for (const StepGeom& g : L.g) {
+    int l = 0;
+    if (cusolverDnDsyevd_bufferSize(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                    (int)g.N, p->Escr, (int)g.N, p->wasc, &l) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return cleanup(HOTRG_ECUDA);
+    if (l > lw) lw = l;
+  }
+  p->lwork = lw;
+  ALC(p->work, (long long)lw);
+  if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
+#undef ALC
+  *out = p;
+  return HOTRG_OK;
+}
+
+void hotrg_plan_destroy(hotrg_plan p) {
+  if (!p) return;
+  if (p->stream) cudaStreamSynchronize(p->stream);
+  else cudaDeviceSynchronize();
+  if (p->solver) cusolverDnDestroy(p->solver);
+  for (auto e : p->ev_pool)
+    if (e) cudaEventDestroy(e);
+  for (void* v : p->allocs) cudaFree(v);
+  delete p;
+}
+
+hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* out_dev) {
+  if (!p || !T0_dev) return fail(p, HOTRG_EINVAL, "null argument");
+  const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
+  p->have_fwd = false;
+  CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  if (T0_dev != p->T[0])
+    CK(cudaMemcpyAsync(p->T[0], T0_dev, sizeof(double) * n0, cudaMemcpyDeviceToDevice, p->stream));
+  hotrg_status r = run_forward(p);
+  if (r != HOTRG_OK) return r;
+  if (out_dev)
+    CK(cudaMemcpyAsync(out_dev, p->out, sizeof(double) * (p->cfg.n_steps + 2),
+                       cudaMemcpyDeviceToDevice, p->stream));
+  p->have_fwd = true;
+  p->fwd_ising = false;
+  return HOTRG_OK;
+}
+
+static hotrg_status copy_out(hotrg_plan p, double* lnz, double* log_norms, int* sign) {
+  std::vector<double> h(p->cfg.n_steps + 2);
+  CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                     p->stream));
+  hotrg_status r = finish_sync(p);
+  if (r != HOTRG_OK) {
+    p->have_fwd = false;
+    return r;
+  }
+  if (lnz) *lnz = h[0];
+  if (sign) *sign = h[1] >= 0 ? 1 : -1;
+  if (log_norms) memcpy(log_norms, h.data() + 2, sizeof(double) * p->cfg.n_steps);
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_forward_tensor(hotrg_plan p, const double* T0_host, double* lnz,
+                                  double* log_norms, int* trace_sign) {
+  if (!p || !T0_host) return fail(p, HOTRG_EINVAL, "null argument");
+  const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
+  for (long long i = 0; i < n0; ++i)
+    if (!std::isfinite(T0_host[i])) return fail(p, HOTRG_EINVAL, "T0 has a non-finite entry");
+  CK(cudaMemcpyAsync(p->T[0], T0_host, sizeof(double) * n0, cudaMemcpyHostToDevice, p->stream));
+  hotrg_status r = hotrg_forward_device(p, p->T[0], nullptr);
+  if (r != HOTRG_OK) return r;
+  return copy_out(p, lnz, log_norms, trace_sign);
+}
+
+hotrg_status hotrg_forward_ising(hotrg_plan p, double beta, double J, double h, double* lnz,
+                                 double* log_norms, int* trace_sign) {
+  if (!p) return HOTRG_EINVAL;
+  if (p->cfg.d0 != 2) return fail(p, HOTRG_EINVAL, "Ising tensor needs d0 == 2");
+  if (!std::isfinite(beta) || !std::isfinite(J) || !std::isfinite(h) || beta * J < 0)
+    return fail(p, HOTRG_EINVAL, "Ising parameters must be finite with beta*J >= 0");
+  CK(ising_t0(beta, J, h, p->T[0], p->dT0, p->stream));
+  hotrg_status r = hotrg_forward_device(p, p->T[0], nullptr);
+  if (r != HOTRG_OK) return r;
+  r = copy_out(p, lnz, log_norms, trace_sign);
+  if (r == HOTRG_OK) p->fwd_ising = true;
+  return r;
+}
+
+hotrg_status hotrg_backward_device(hotrg_plan p, double* grad_dev) {
+  if (!p) return HOTRG_EINVAL;
+  if (!p->cfg.want_grad) return fail(p, HOTRG_ESTATE, "plan created with want_grad = 0");
+  if (!p->have_fwd) return fail(p, HOTRG_ESTATE, "backward needs a forward first");
+  CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  hotrg_status r = run_backward(p);
+  if (r != HOTRG_OK) return r;
+  if (grad_dev) {
+    const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
+    CK(cudaMemcpyAsync(grad_dev, p->Ecur, sizeof(double) * n0, cudaMemcpyDeviceToDevice,
+                       p->stream));
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_backward(hotrg_plan p, double* grad, double* dbeta) {
+  if (!p) return HOTRG_EINVAL;
+  if (dbeta && !p->fwd_ising) return fail(p, HOTRG_ESTATE, "d/dbeta needs hotrg_forward_ising");
+  hotrg_status r = hotrg_backward_device(p, nullptr);
+  if (r != HOTRG_OK) return r;
+  const int n0 = p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
+  if (dbeta) CK(dot_small(p->Ecur, p->dT0, n0, p->scal + 2, p->stream));
+  std::vector<double> h(n0);
+  double db = 0;
+  CK(cudaMemcpyAsync(h.data(), p->Ecur, sizeof(double) * n0, cudaMemcpyDeviceToHost, p->stream));
+  if (dbeta) CK(cudaMemcpyAsync(&db, p->scal + 2, sizeof(double), cudaMemcpyDeviceToHost, p->stream));
+  r = finish_sync(p);
+  if (r != HOTRG_OK) return r;
+  if (grad) memcpy(grad, h.data(), sizeof(double) * n0);
+  if (dbeta) *dbeta = db;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_sync(hotrg_plan p) {
+  if (!p) return HOTRG_EINVAL;
+  return finish_sync(p);
+}
+
+hotrg_status hotrg_diagnostics(hotrg_plan p, double* trunc, double* gap, int* is_split) {
+  if (!p) return HOTRG_EINVAL;
+  const int n = p->cfg.n_steps;
+  if (trunc) CK(cudaMemcpy(trunc, p->dtrunc, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  if (gap) CK(cudaMemcpy(gap, p->dgap, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  if (is_split)
+    for (int k = 0; k < n; ++k) is_split[k] = p->L.g[k].split ? 1 : 0;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_step_dims(hotrg_plan p, int step, int* X, int* Y, int* Xp) {
+  if (!p || step < 1 || step > p->cfg.n_steps) return HOTRG_EINVAL;
+  const StepGeom& g = p->L.g[step - 1];
+  if (X) *X = g.X;
+  if (Y) *Y = g.Y;
+  if (Xp) *Xp = g.Xp;
+  return HOTRG_OK;
+}
+
+const char* hotrg_status_string(hotrg_status s) {
+  switch (s) {
+    case HOTRG_OK: return "ok";
+    case HOTRG_EINVAL: return "invalid argument";
+    case HOTRG_ENOMEM: return "out of device memory";
+    case HOTRG_ECUDA: return "CUDA error";
+    case HOTRG_ENOTCONV: return "eigensolver did not converge";
+    case HOTRG_ENONFINITE: return "non-finite norm or trace";
+    case HOTRG_ETIMEOUT: return "device wait timed out";
+    case HOTRG_ESTATE: return "call out of order";
+    case HOTRG_EUNSUPPORTED: return "unsupported on this device";
+  }
+  return "unknown status";
+}
+
+const char* hotrg_last_error(hotrg_plan p) { return p ? p->last_error.c_str() : "null plan"; }
+
+hotrg_status hotrg_device_supports_split(void) {
+  int dev = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    cudaGetLastError();
+    return HOTRG_ECUDA;
+  }
+  return (prop.major == 10 && prop.minor == 3) ? HOTRG_OK : HOTRG_EUNSUPPORTED;
+}
+
+hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
+                                    const double* B, double* C) {
+  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || (planes != 2 && planes != 3) || !A || !B || !C)
+    return HOTRG_EINVAL;
+  hotrg_status status = HOTRG_OK;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  __nv_bfloat16 *pa = nullptr, *pb = nullptr;
+  int* err = nullptr;
+  const long long sa = round_up((long long)M * K, 64), sb = round_up((long long)N * K, 64);
+  int sms = 152, dev = 0, e = 0;
+  cudaDeviceProp prop;
+  TcGemm g;
+  memset(&g, 0, sizeof(g));
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess) {
+    status = HOTRG_ECUDA;
+    goto done;
+  }
+  sms = prop.multiProcessorCount;
+  if (cudaMalloc(&dA, sizeof(double) * M * (size_t)K) != cudaSuccess ||
+      cudaMalloc(&dB, sizeof(double) * N * (size_t)K) != cudaSuccess ||
+      cudaMalloc(&dC, sizeof(double) * M * (size_t)N) != cudaSuccess ||
+      cudaMalloc(&pa, 2 * sa * planes) != cudaSuccess ||
+      cudaMalloc(&pb, 2 * sb * planes) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    status = HOTRG_ENOMEM;
+    goto done;
+  }
+  cudaMemcpy(dA, A, sizeof(double) * M * (size_t)K, cudaMemcpyHostToDevice);
+  cudaMemcpy(dB, B, sizeof(double) * N * (size_t)K, cudaMemcpyHostToDevice);
+  cudaMemset(err, 0, sizeof(int));
+  gather_split(dA, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, 0, sms);
+  gather_split(dB, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, 0, sms);
+  tc_set_pairs(g, planes);
+  g.M = M; g.N = N; g.K = K; g.kchunk = kchunk;
+  g.cm = map_lin(N); g.cn = map_lin(1);
+  g.out_mode = kOutF64; g.out_planes = 1; g.C = dC; g.alpha = 1.f; g.err = err;
+  g.c_lim = (long long)M * N;
+  if (tc_gemm(opnd(pa, M, K, planes, sa), opnd(pb, N, K, planes, sb), g, 0, sms) != cudaSuccess) {
+    status = HOTRG_ECUDA;
+    goto done;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) { status = HOTRG_ECUDA; goto done; }
+  cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e & kErrTimeout) { status = HOTRG_ETIMEOUT; goto done; }
+  if (e) { status = HOTRG_ECUDA; goto done; }
+  if (cudaMemcpy(C, dC, sizeof(double) * M * (size_t)N, cudaMemcpyDeviceToHost) != cudaSuccess)
+    status = HOTRG_ECUDA;
+done:
+  cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(pa); cudaFree(pb); cudaFree(err);
+  cudaGetLastError();
+  return status;
+}
+
+hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const double* B, double* C) {
+  if (M < 1 || N < 1 || K < 1 || !A || !B || !C) return HOTRG_EINVAL;
+  hotrg_status status = HOTRG_OK;
+  double *dA = nullptr, *dB = nullptr, *dC = nullptr;
+  int* err = nullptr;
+  int dev = 0, e = 0;
+  cudaDeviceProp prop;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
+    return HOTRG_ECUDA;
+  if (cudaMalloc(&dA, sizeof(double) * M * (size_t)K) != cudaSuccess ||
+      cudaMalloc(&dB, sizeof(double) * N * (size_t)K) != cudaSuccess ||
+      cudaMalloc(&dC, sizeof(double) * M * (size_t)N) != cudaSuccess ||
+      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    status = HOTRG_ENOMEM;
+  } else {
+    cudaMemcpy(dA, A, sizeof(double) * M * (size_t)K, cudaMemcpyHostToDevice);
+    cudaMemcpy(dB, B, sizeof(double) * N * (size_t)K, cudaMemcpyHostToDevice);
+    cudaMemset(err, 0, sizeof(int));
+    GemmF64 g;
+    g.A = dA; g.am = map_lin(K); g.ak = map_lin(1);
+    g.B = dB; g.bn = map_lin(K); g.bk = map_lin(1);
+    g.C = dC; g.cm = map_lin(N); g.cn = map_lin(1);
+    g.M = M; g.N = N; g.K = K; g.alpha = 1.0; g.beta = 0.0; g.a_kfast = 1; g.b_kfast = 1;
+    g.a_lim = (long long)M * K; g.b_lim = (long long)N * K; g.c_lim = (long long)M * N;
+    g.err = err;
+    if (gemm_f64(g, 0, prop.multiProcessorCount) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
+      status = HOTRG_ECUDA;
+    else if (cudaMemcpy(C, dC, sizeof(double) * M * (size_t)N, cudaMemcpyDeviceToHost) != cudaSuccess)
+      status = HOTRG_ECUDA;
+    else if (cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess || e)
+      status = HOTRG_ECUDA;
+  }
+  cudaFree(dA); cudaFree(dB); cudaFree(dC); cudaFree(err);
+  cudaGetLastError();
+  return status;
+}
+
+}  // extern "C"

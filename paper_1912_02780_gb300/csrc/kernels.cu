@@ -1,0 +1,380 @@
+// Memory-bound helper kernels of the HOTRG path: operand preparation
+// (gather + bf16 split), the Ising site tensor, FP64 norms and traces, the
+// eigenvector post-processing and the element-wise parts of the backward.
+#include <math.h>
+#include "kernels.h"
+
+namespace hotrg {
+
+namespace {
+
+__device__ __forceinline__ long long gtid() {
+  return blockIdx.x * (long long)blockDim.x + threadIdx.x;
+}
+__device__ __forceinline__ long long gstride() { return (long long)gridDim.x * blockDim.x; }
+
+int blocks_for(long long n, int num_sms) {
+  long long b = (n + 255) / 256;
+  long long cap = 16LL * num_sms;
+  if (b > cap) b = cap;
+  if (b < 1) b = 1;
+  return (int)b;
+}
+
+// dst plane p, element (r, k) at dst + p * plane_stride + r * K + k.
+__global__ void gather_split_kernel(const double* __restrict__ src, long long src_lim, IMap rm,
+                                    IMap km, int rows, int K, int nplanes,
+                                    long long plane_stride, __nv_bfloat16* __restrict__ dst,
+                                    int* err) {
+  const long long total = (long long)rows * K;
+  for (long long i = gtid(); i < total; i += gstride()) {
+    int r = (int)(i / K), k = (int)(i - (long long)r * K);
+    const long long off = imap(rm, r) + imap(km, k);
+    double v = 0.0;
+    if (off >= 0 && off < src_lim) v = src[off];
+    else atomicOr(err, kErrBounds);
+    __nv_bfloat16 b[3];
+    split_bf16_d(v, nplanes, b);
+    dst[i] = b[0];
+    if (nplanes > 1) dst[plane_stride + i] = b[1];
+    if (nplanes > 2) dst[2 * plane_stride + i] = b[2];
+  }
+}
+
+// T0 and dT0/dbeta of the Ising model (one tensor per spin).
+__global__ void ising_t0_kernel(double beta, double J, double h, double* T0, double* dT0) {
+  int idx = threadIdx.x;   // 16 threads: (l, r, u, d) bits
+  if (idx >= 16) return;
+  const double k = beta * J;
+  const double ch = cosh(k), sh = sinh(k);
+  const double a = sqrt(ch), b = sqrt(sh);
+  const double da = J * sh / (2.0 * a);
+  const double db = (b > 0.0) ? J * ch / (2.0 * b) : 0.0;
+  int leg[4] = {(idx >> 3) & 1, (idx >> 2) & 1, (idx >> 1) & 1, idx & 1};
+  double t = 0.0, dt = 0.0;
+  for (int si = 0; si < 2; ++si) {
+    const double s = si == 0 ? 1.0 : -1.0;
+    const double e = exp(beta * h * s), de = h * s * e;
+    double W[4], dW[4];
+    for (int q = 0; q < 4; ++q) {
+      W[q] = leg[q] == 0 ? a : s * b;
+      dW[q] = leg[q] == 0 ? da : s * db;
+    }
+    const double prod = W[0] * W[1] * W[2] * W[3];
+    t += e * prod;
+    double dprod = dW[0] * W[1] * W[2] * W[3] + W[0] * dW[1] * W[2] * W[3] +
+                   W[0] * W[1] * dW[2] * W[3] + W[0] * W[1] * W[2] * dW[3];
+    dt += de * prod + e * dprod;
+  }
+  T0[idx] = t;
+  if (dT0) dT0[idx] = dt;
+}
+
+// Deterministic FP64 sum of squares: per-block partials, then one block.
+__global__ void sumsq_partial_kernel(const double* __restrict__ x, long long n,
+                                     double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long i = gtid(); i < n; i += gstride()) s = fma(x[i], x[i], s);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ double ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+// c = sqrt(sum partials); log_norm = ln c; inv = 1/c stored in scal[0].
+__global__ void norm_finalize_kernel(const double* __restrict__ partial, int np,
+                                     double* __restrict__ log_norm, double* __restrict__ inv,
+                                     int* err) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < np; i += blockDim.x) s += partial[i];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = (threadIdx.x < (blockDim.x >> 5)) ? ws[threadIdx.x] : 0.0;
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) {
+      double c = sqrt(s);
+      if (!(c > 0.0) || !isfinite(c)) {
+        atomicOr(err, kErrNonFinite);
+        c = 1.0;
+      }
+      *log_norm = log(c);
+      *inv = 1.0 / c;
+    }
+  }
+}
+
+__global__ void scale_kernel(double* __restrict__ x, long long n, const double* __restrict__ s) {
+  const double f = *s;
+  for (long long i = gtid(); i < n; i += gstride()) x[i] *= f;
+}
+
+// out = [lnz, sign, log_norms...]; T stored as [a][a][b][b]-traceable tensor
+// with leg dims (P, P, Q, Q).
+__global__ void trace_lnz_kernel(const double* __restrict__ T, int P, int Q,
+                                 const double* __restrict__ log_norms, int n,
+                                 double* __restrict__ out, double* __restrict__ trace_out,
+                                 int* err) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (int i = threadIdx.x; i < P * Q; i += blockDim.x) {
+    int a = i / Q, b = i % Q;
+    s += T[((long long)(a * P + a) * Q + b) * Q + b];
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double tr = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) tr += ws[w];
+    double acc = 0.0, scale = 1.0;
+    for (int k = 0; k < n; ++k) {
+      scale *= 0.5;
+      acc += log_norms[k] * scale;
+    }
+    if (!(fabs(tr) > 0.0) || !isfinite(tr)) atomicOr(err, kErrNonFinite);
+    out[0] = acc + log(fabs(tr)) * scale;
+    out[1] = tr >= 0.0 ? 1.0 : -1.0;
+    for (int k = 0; k < n; ++k) out[2 + k] = log_norms[k];
+    *trace_out = tr;
+  }
+}
+
+// Eigen post-processing.  cuSOLVER returns eigenvalues ascending and the
+// eigenvectors as the columns of a column-major matrix, i.e. eigenvector a is
+// the contiguous row a of `asc`.  Write them descending: row alpha of `desc`
+// is eigenvector N-1-alpha, flipped so that its largest-magnitude component
+// (lowest index on ties) is positive.  One block per eigenvector.
+__global__ void eig_desc_kernel(const double* __restrict__ asc, const double* __restrict__ w_asc,
+                                int N, int rows_out, double* __restrict__ desc,
+                                double* __restrict__ lam_desc) {
+  const int alpha = blockIdx.x;
+  if (alpha >= rows_out) return;
+  const double* src = asc + (long long)(N - 1 - alpha) * N;
+  double best = -1.0;
+  int bi = 0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    double v = fabs(src[i]);
+    if (v > best) { best = v; bi = i; }
+  }
+  __shared__ double sb[256];
+  __shared__ int si[256];
+  sb[threadIdx.x] = best;
+  si[threadIdx.x] = bi;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      double b2 = sb[threadIdx.x + o];
+      int i2 = si[threadIdx.x + o];
+      if (b2 > sb[threadIdx.x] || (b2 == sb[threadIdx.x] && i2 < si[threadIdx.x])) {
+        sb[threadIdx.x] = b2;
+        si[threadIdx.x] = i2;
+      }
+    }
+    __syncthreads();
+  }
+  const double sgn = src[si[0]] < 0.0 ? -1.0 : 1.0;
+  double* dst = desc + (long long)alpha * N;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = sgn * src[i];
+  if (alpha == 0)
+    for (int i = threadIdx.x; i < N; i += blockDim.x) lam_desc[i] = w_asc[N - 1 - i];
+}
+
+// trunc_err = sum(lam[Dp:]) / sum(lam); gap = (lam[Dp-1] - lam[Dp]) / lam[0].
+__global__ void eig_diag_kernel(const double* __restrict__ lam, int N, int Dp, double* trunc,
+                                double* gap) {
+  __shared__ double s_all[256], s_cut[256];
+  double a = 0.0, c = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    a += lam[i];
+    if (i >= Dp) c += lam[i];
+  }
+  s_all[threadIdx.x] = a;
+  s_cut[threadIdx.x] = c;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) {
+      s_all[threadIdx.x] += s_all[threadIdx.x + o];
+      s_cut[threadIdx.x] += s_cut[threadIdx.x + o];
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    *trunc = s_all[0] != 0.0 ? s_cut[0] / s_all[0] : 0.0;
+    *gap = (Dp < N && lam[0] != 0.0) ? (lam[Dp - 1] - lam[Dp]) / lam[0] : 0.0;
+  }
+}
+
+__global__ void eigh_info_kernel(const int* info, int* err) {
+  if (threadIdx.x == 0 && *info != 0) atomicOr(err, kErrEigh);
+}
+
+// Backward seed: E = delta(a,a') delta(b,b') / trace on a (P, P, Q, Q) tensor.
+__global__ void seed_kernel(double* __restrict__ E, int P, int Q, const double* __restrict__ tr) {
+  const long long n = (long long)P * P * Q * Q;
+  const double inv = 1.0 / *tr;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    int d = (int)(i % Q);
+    int u = (int)((i / Q) % Q);
+    int r = (int)((i / ((long long)Q * Q)) % P);
+    int l = (int)(i / ((long long)Q * Q * P));
+    E[i] = (l == r && u == d) ? inv : 0.0;
+  }
+}
+
+// F o S for the eigensolve adjoint: S[j][k] (j discarded, k kept) times
+// (lam_k - lam_j) / ((lam_k - lam_j)^2 + eta), eta = eta_rel * lam_0^2.
+__global__ void eigh_adj_scale_kernel(double* __restrict__ S, int nd, int Dp,
+                                      const double* __restrict__ lam, double eta_rel) {
+  const double eta = eta_rel * lam[0] * lam[0];
+  const long long n = (long long)nd * Dp;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    int j = (int)(i / Dp), k = (int)(i % Dp);
+    double d = lam[k] - lam[Dp + j];
+    S[i] *= d / (d * d + eta);
+  }
+}
+
+// G <- (G + G^T) / 2 in place (N x N).
+__global__ void symmetrize_kernel(double* __restrict__ G, int N) {
+  const long long n = (long long)N * N;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    int r = (int)(i / N), c = (int)(i % N);
+    if (c > r) {
+      double a = G[i], b = G[(long long)c * N + r];
+      double m = 0.5 * (a + b);
+      G[i] = m;
+      G[(long long)c * N + r] = m;
+    }
+  }
+}
+
+__global__ void scale_copy_kernel(const double* __restrict__ x, double* __restrict__ y, long long n,
+                                  double a) {
+  for (long long i = gtid(); i < n; i += gstride()) y[i] = a * x[i];
+}
+
+__global__ void scale_exp_neg_kernel(double* __restrict__ x, long long n,
+                                     const double* __restrict__ logc) {
+  const double f = exp(-*logc);
+  for (long long i = gtid(); i < n; i += gstride()) x[i] *= f;
+}
+
+__global__ void dot16_kernel(const double* __restrict__ a, const double* __restrict__ b, int n,
+                             double* out) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) s = fma(a[i], b[i], s);
+    *out = s;
+  }
+}
+
+}  // namespace
+
+cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                         int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                         cudaStream_t st, int sms) {
+  long long n = (long long)rows * K;
+  if (n == 0) return cudaSuccess;
+  if (n > plane_stride) return cudaErrorInvalidValue;
+  count_launch();
+  gather_split_kernel<<<blocks_for(n, sms), 256, 0, st>>>(src, src_lim, rm, km, rows, K, nplanes,
+                                                          plane_stride, dst, err);
+  return cudaGetLastError();
+}
+
+cudaError_t ising_t0(double beta, double J, double h, double* T0, double* dT0, cudaStream_t st) {
+  count_launch();
+  ising_t0_kernel<<<1, 32, 0, st>>>(beta, J, h, T0, dT0);
+  return cudaGetLastError();
+}
+
+cudaError_t frob_normalize(double* x, long long n, double* partial, int max_partial,
+                           double* log_norm, double* inv_scratch, int* err, cudaStream_t st,
+                           int sms) {
+  int b = blocks_for(n, sms);
+  if (b > max_partial) b = max_partial;
+  count_launch();
+  sumsq_partial_kernel<<<b, 256, 0, st>>>(x, n, partial);
+  count_launch();
+  norm_finalize_kernel<<<1, 256, 0, st>>>(partial, b, log_norm, inv_scratch, err);
+  count_launch();
+  scale_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, n, inv_scratch);
+  return cudaGetLastError();
+}
+
+cudaError_t trace_lnz(const double* T, int P, int Q, const double* log_norms, int n, double* out,
+                      double* trace_out, int* err, cudaStream_t st) {
+  count_launch();
+  trace_lnz_kernel<<<1, 256, 0, st>>>(T, P, Q, log_norms, n, out, trace_out, err);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int rows_out, double* desc,
+                     double* lam_desc, cudaStream_t st) {
+  count_launch();
+  eig_desc_kernel<<<rows_out, 256, 0, st>>>(asc, w_asc, N, rows_out, desc, lam_desc);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_diag(const double* lam, int N, int Dp, double* trunc, double* gap,
+                     cudaStream_t st) {
+  count_launch();
+  eig_diag_kernel<<<1, 256, 0, st>>>(lam, N, Dp, trunc, gap);
+  return cudaGetLastError();
+}
+
+cudaError_t eigh_info_check(const int* info, int* err, cudaStream_t st) {
+  count_launch();
+  eigh_info_kernel<<<1, 32, 0, st>>>(info, err);
+  return cudaGetLastError();
+}
+
+cudaError_t seed_trace_adjoint(double* E, int P, int Q, const double* tr, cudaStream_t st,
+                               int sms) {
+  count_launch();
+  seed_kernel<<<blocks_for((long long)P * P * Q * Q, sms), 256, 0, st>>>(E, P, Q, tr);
+  return cudaGetLastError();
+}
+
+cudaError_t eigh_adj_scale(double* S, int nd, int Dp, const double* lam, double eta_rel,
+                           cudaStream_t st, int sms) {
+  count_launch();
+  eigh_adj_scale_kernel<<<blocks_for((long long)nd * Dp, sms), 256, 0, st>>>(S, nd, Dp, lam,
+                                                                           eta_rel);
+  return cudaGetLastError();
+}
+
+cudaError_t symmetrize(double* G, int N, cudaStream_t st, int sms) {
+  count_launch();
+  symmetrize_kernel<<<blocks_for((long long)N * N, sms), 256, 0, st>>>(G, N);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_copy(const double* x, double* y, long long n, double a, cudaStream_t st,
+                       int sms) {
+  count_launch();
+  scale_copy_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, y, n, a);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream_t st, int sms) {
+  count_launch();
+  scale_exp_neg_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, n, logc);
+  return cudaGetLastError();
+}
+
+cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st) {
+  count_launch();
+  dot16_kernel<<<1, 32, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+}  // namespace hotrg

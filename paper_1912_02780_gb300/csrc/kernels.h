@@ -1,0 +1,32 @@
+// Launchers of the memory-bound helper kernels (see kernels.cu).
+#pragma once
+#include "common.cuh"
+
+namespace hotrg {
+
+// dst planes [p][r][K] = bf16 split of src[rm(r) + km(k)]; source offsets at
+// or beyond src_lim are read as 0 and flagged (kErrBounds).
+cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                         int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                         cudaStream_t st, int sms);
+cudaError_t ising_t0(double beta, double J, double h, double* T0, double* dT0, cudaStream_t st);
+// x <- x / ||x||_F (FP64, deterministic), *log_norm = ln ||x||_F.
+cudaError_t frob_normalize(double* x, long long n, double* partial, int max_partial,
+                           double* log_norm, double* inv_scratch, int* err, cudaStream_t st,
+                           int sms);
+cudaError_t trace_lnz(const double* T, int P, int Q, const double* log_norms, int n, double* out,
+                      double* trace_out, int* err, cudaStream_t st);
+cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int rows_out, double* desc,
+                     double* lam_desc, cudaStream_t st);
+cudaError_t eig_diag(const double* lam, int N, int Dp, double* trunc, double* gap, cudaStream_t st);
+cudaError_t eigh_info_check(const int* info, int* err, cudaStream_t st);
+cudaError_t seed_trace_adjoint(double* E, int P, int Q, const double* tr, cudaStream_t st, int sms);
+cudaError_t eigh_adj_scale(double* S, int nd, int Dp, const double* lam, double eta_rel,
+                           cudaStream_t st, int sms);
+cudaError_t symmetrize(double* G, int N, cudaStream_t st, int sms);
+cudaError_t scale_copy(const double* x, double* y, long long n, double a, cudaStream_t st, int sms);
+// x <- x * exp(-*logc)  (divide by a norm whose log lives on the device)
+cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream_t st, int sms);
+cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st);
+
+}  // namespace hotrg
