@@ -175,6 +175,27 @@ hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk,
                                     const double* B, double* C);
 hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const double* B, double* C);
 
+/* Allocation-free variant of hotrg_gemm_split_check (the paper has no
+ * counterpart; this is a library facility).  For callers that may not call
+ * cudaMalloc: their device memory is owned by another allocator (a
+ * framework's caching allocator or a fixed arena), or they run latency-bound
+ * loops where an allocation would synchronise the device or could fail
+ * mid-request.  The caller passes device buffers: A_dev (M x K), B_dev
+ * (N x K), C_dev (M x N), row-major float64; C = A B^T as in
+ * hotrg_gemm_split_check.  Scratch (the bf16 operand planes and an error
+ * word) lives in a static device array of 8 MiB that every GPU loading this
+ * library holds until process exit; sizes with
+ * 256 + 2 * planes * (roundup64(M*K) + roundup64(N*K)) > 8 MiB are rejected
+ * with HOTRG_EINVAL.  Nothing is allocated: no cudaMalloc, no cudaFree.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ * default stream) and the call waits for it.  All calls share the one array,
+ * so calls that overlap on the GPU (other threads, other streams) race. */
+hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes, int kchunk,
+                                      const double* A_dev, const double* B_dev, double* C_dev,
+                                      void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,7 @@ EXPORTS = (
     "hotrg_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
+    "hotrg_gemm_split_noalloc",
 )
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
@@ -92,6 +93,7 @@ def lib() -> ctypes.CDLL:
     L.hotrg_profile_read.argtypes = [vp, _dp, _ip]
     L.hotrg_kernel_launches.argtypes = []
     L.hotrg_kernel_launches.restype = ctypes.c_ulonglong
+    L.hotrg_gemm_split_noalloc.argtypes = [ctypes.c_int] * 5 + [vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
                         "hotrg_last_error", "hotrg_kernel_launches"):
