@@ -169,6 +169,21 @@ __device__ __forceinline__ void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// Named barrier with an AND-reduction of `pred` over the participating threads,
+// so that every epilogue warp takes the same branch after a failed wait.
+__device__ __forceinline__ bool named_bar_and(int id, int count, bool pred) {
+  uint32_t r;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "setp.ne.u32 p, %1, 0;\n\t"
+      "barrier.red.and.pred q, %2, %3, p;\n\t"
+      "selp.u32 %0, 1, 0, q;\n\t}\n"
+      : "=r"(r)
+      : "r"((uint32_t)pred), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = a + b;
   float bb = s - a;
@@ -181,15 +196,16 @@ struct Cfg {
   static constexpr int kBPlane = BN * BK * 2;
   static constexpr int kStage = NP * (kAPlane + kBPlane);
   static constexpr int kStages = (200 * 1024 / kStage) > 4 ? 4 : (200 * 1024 / kStage);
+  static constexpr int kEpiWarps = 8;                    // 2 warps per TMEM lane quadrant
+  static constexpr int kThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
+  static constexpr int kCols = BN / 2;                   // columns per epilogue thread
   static constexpr int kBars = 2 * kStages + 5;
   static constexpr int kSmem = 1024 + kStages * kStage + kBars * 8 + BN * 8 + BN / 16 * 4 + 16;
-  static constexpr int kTmemCols = (4 * BN <= 512) ? 4 * BN : 2 * BN;
+  // TMEM: per buffer (2) an exact hi*hi accumulator and a "rest" accumulator, BN columns each.
+  static constexpr int kTmemCols = 4 * BN;
   static_assert(kStages >= 2, "need at least two pipeline stages");
+  static_assert(kTmemCols <= 512, "TMEM holds 512 columns");
 };
-
-// 16 consecutive output columns of one row.  When their offsets are
-// contiguous and aligned (flag `contig`, precomputed per tile) the row segment
-// is written with 16-byte vector stores, otherwise element by element.
 template <int BN, int NP>
 __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff,
                                                  const long long* cn_s, int contig, int cc,
@@ -269,7 +285,7 @@ __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff
 }
 
 template <int BN, int NP>
-__global__ void __launch_bounds__(192, 1)
+__global__ void __launch_bounds__(Cfg<BN, NP>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcGemm p) {
   using C = Cfg<BN, NP>;
@@ -282,6 +298,7 @@ __global__ void __launch_bounds__(192, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cv_s + BN / 16);
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
+  const int kProducer = C::kEpiWarps, kMma = C::kEpiWarps + 1;
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (C::kStages + s); };
@@ -294,14 +311,14 @@ __global__ void __launch_bounds__(192, 1)
     return smem0 + s * C::kStage + NP * C::kAPlane + pl * C::kBPlane;
   };
 
-  if (warp == 4 && lane == 0) {
+  if (warp == kProducer && lane == 0) {
     for (int s = 0; s < C::kStages; ++s) {
       mbar_init(full_bar(s), 1);
       mbar_init(empty_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), 4);
+      mbar_init(tempty_bar(a), C::kEpiWarps);
     }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -309,7 +326,7 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmA) : "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
   }
-  if (warp == 5) {
+  if (warp == kMma) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      smem_u32(tmem_slot)),
                  "r"(C::kTmemCols)
@@ -326,13 +343,15 @@ __global__ void __launch_bounds__(192, 1)
   const int KB = (p.K + BK - 1) / BK;
   const int kchunk = p.kchunk < 1 ? KB : (p.kchunk > KB ? KB : p.kchunk);
   const int nchunks = (KB + kchunk - 1) / kchunk;
-  const bool compensated = (nchunks > 1) && (4 * BN <= 512);
 
-  if (warp == 4) {
+  if (warp == kProducer) {
     if (lane == 0) {
       int s = 0;
       uint32_t ph = 0;
       bool ok = true;
+      int issued[C::kStages];
+      uint32_t last_par[C::kStages];
+      for (int i = 0; i < C::kStages; ++i) { issued[i] = 0; last_par[i] = 0; }
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         const int mt = (int)(t / NT), nt = (int)(t % NT);
         for (int kb = 0; kb < KB; ++kb) {
@@ -344,15 +363,18 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
           for (int pl = 0; pl < NP; ++pl)
             tma_load_3d(b_tile(s, pl), &tmB, full_bar(s), kb * BK, nt * BN, pl);
+          issued[s] = 1;
+          last_par[s] = ph;
           if (++s == C::kStages) { s = 0; ph ^= 1u; }
         }
       }
       if (!ok) {
         // Let copies already in flight land before the CTA can exit.
-        for (int s2 = 0; s2 < C::kStages; ++s2) mbar_wait(full_bar(s2), 0, p.err);
+        for (int s2 = 0; s2 < C::kStages; ++s2)
+          if (issued[s2]) mbar_wait(full_bar(s2), last_par[s2], p.err);
       }
     }
-  } else if (warp == 5) {
+  } else if (warp == kMma) {
     if (lane == 0) {
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
       int s = 0;
@@ -364,17 +386,21 @@ __global__ void __launch_bounds__(192, 1)
         for (int c = 0; c < nchunks && ok; ++c) {
           if (!mbar_wait(tempty_bar(acc), acc_ph ^ 1u, p.err)) { ok = false; break; }
           tc_fence_after();
-          const uint32_t d = tmem_base + (uint32_t)(acc * BN);
+          const uint32_t d_hh = tmem_base + (uint32_t)(acc * 2 * BN);
+          const uint32_t d_rest = d_hh + BN;
           const int kb0 = c * kchunk, kb1 = min(KB, kb0 + kchunk);
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(full_bar(s), ph, p.err)) { ok = false; break; }
             tc_fence_after();
             for (int q = 0; q < p.npairs; ++q) {
+              // product 0 (hi * hi) has its own, exactly accumulated, TMEM buffer
+              const uint32_t d = (q == 0) ? d_hh : d_rest;
+              const bool first = (kb == kb0) && (q <= 1);
               const uint32_t a0 = a_tile(s, p.pa[q]), b0 = b_tile(s, p.pb[q]);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 tc_mma(d, sdesc_sw128(a0 + kk * 32), sdesc_sw128(b0 + kk * 32), idesc,
-                       (kb > kb0 || q > 0 || kk > 0) ? 1u : 0u);
+                       (first && kk == 0) ? 0u : 1u);
               }
             }
             tc_commit(empty_bar(s));
@@ -390,81 +416,92 @@ __global__ void __launch_bounds__(192, 1)
       mbar_wait(drain_bar, 0, p.err);
     }
   } else {
-    // Epilogue warps 0..3: warp w owns TMEM lanes [32w, 32w + 32) = tile rows.
+    // Epilogue warps 0..7: warp w owns TMEM lanes [32 (w % 4), +32) (tile rows)
+    // and columns [(w / 4) BN / 2, +BN / 2).  Chunk sums hh + rest are added
+    // into a float-float running sum held in registers.
+    constexpr int kEpiThreads = C::kEpiWarps * 32;
     int acc = 0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    const int row = warp * 32 + lane;
-    const uint32_t lane_base = tmem_base + ((uint32_t)(warp * 32) << 16);
+    const int quad = warp & 3, half = warp >> 2;
+    const int row = quad * 32 + lane;
+    const int col0 = half * C::kCols;
+    const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
+    float rhi[C::kCols], rlo[C::kCols];
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
       const int mt = (int)(t / NT), nt = (int)(t % NT);
       const int m0 = mt * BM, n0 = nt * BN;
-      named_bar(1, 128);
-      for (int j = threadIdx.x; j < BN; j += 128)
-        cn_s[j] = (n0 + j < p.N) ? imap(p.cn, n0 + j) : -1;
-      named_bar(1, 128);
-      if (threadIdx.x < BN / 16) {
-        int ok = cn_s[threadIdx.x * 16] >= 0;
-        for (int j = 1; j < 16 && ok; ++j)
-          ok = (cn_s[threadIdx.x * 16 + j] == cn_s[threadIdx.x * 16 + j - 1] + 1);
-        cv_s[threadIdx.x] = ok;
-      }
-      named_bar(1, 128);
       const int m = m0 + row;
       const bool mok = m < p.M;
       const long long coff = mok ? imap(p.cm, m) : 0;
       for (int c = 0; c < nchunks; ++c) {
-        if (!mbar_wait(tfull_bar(acc), acc_ph, p.err)) { ok = false; break; }
+        // warp-uniform wait: a lane that gave up stops its whole warp
+        const bool w_ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(acc), acc_ph, p.err));
+        if (!w_ok) { ok = false; break; }
         tc_fence_after();
-        const uint32_t tacc = lane_base + (uint32_t)(acc * BN);
-        const uint32_t thi = lane_base + (uint32_t)(2 * BN), tlo = thi + BN;
-        const bool last = (c == nchunks - 1);
-        for (int cc = 0; cc < BN; cc += 16) {
-          float v[16], hi[16], lo[16];
-          tmem_ld16(tacc + cc, v);
-          if (compensated && c > 0) {
-            tmem_ld16(thi + cc, hi);
-            tmem_ld16(tlo + cc, lo);
-            tmem_ld_wait();
+        const uint32_t thh = lane_base + (uint32_t)(acc * 2 * BN + col0);
+        const uint32_t trs = thh + BN;
 #pragma unroll
-            for (int j = 0; j < 16; ++j) {
-              float s, e;
-              two_sum(hi[j], v[j], s, e);
-              e += lo[j];
-              hi[j] = s + e;
-              lo[j] = e - (hi[j] - s);
+        for (int g = 0; g < C::kCols / 16; ++g) {
+          float a[16], b[16];
+          tmem_ld16(thh + g * 16, a);
+          tmem_ld16(trs + g * 16, b);
+          tmem_ld_wait();
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            float s, e;
+            two_sum(a[j], b[j], s, e);
+            if (c == 0) {
+              rhi[g * 16 + j] = s;
+              rlo[g * 16 + j] = e;
+            } else {
+              float u, f;
+              two_sum(rhi[g * 16 + j], s, u, f);
+              f += rlo[g * 16 + j] + e;
+              rhi[g * 16 + j] = u + f;
+              rlo[g * 16 + j] = f - (rhi[g * 16 + j] - u);
             }
-          } else {
-            tmem_ld_wait();
-#pragma unroll
-            for (int j = 0; j < 16; ++j) { hi[j] = v[j]; lo[j] = 0.f; }
-          }
-          if (compensated && !last) {
-            tmem_st16(thi + cc, hi);
-            tmem_st16(tlo + cc, lo);
-          } else if (last && mok) {
-            store_tile_chunk<BN, NP>(p, coff, cn_s, cv_s[cc / 16], cc, hi, lo);
           }
         }
-        if (compensated && !last) tmem_st_wait();
         tc_fence_before();
         __syncwarp();
         if (lane == 0) mbar_arrive(tempty_bar(acc));
         if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
       }
+      // column offsets of this tile (shared by the 8 epilogue warps); the
+      // AND-barrier also makes every epilogue warp stop together after a failure
+      ok = named_bar_and(1, kEpiThreads, ok);
+      if (!ok) break;
+      for (int j = threadIdx.x; j < BN; j += kEpiThreads)
+        cn_s[j] = (n0 + j < p.N) ? imap(p.cn, n0 + j) : -1;
+      named_bar(1, kEpiThreads);
+      if (threadIdx.x < BN / 16) {
+        int okc = cn_s[threadIdx.x * 16] >= 0;
+        for (int j = 1; j < 16 && okc; ++j)
+          okc = (cn_s[threadIdx.x * 16 + j] == cn_s[threadIdx.x * 16 + j - 1] + 1);
+        cv_s[threadIdx.x] = okc;
+      }
+      named_bar(1, kEpiThreads);
+      if (mok) {
+#pragma unroll
+        for (int g = 0; g < C::kCols / 16; ++g) {
+          const int cc = col0 + g * 16;
+          store_tile_chunk<BN, NP>(p, coff, cn_s, cv_s[cc / 16], cc, rhi + g * 16, rlo + g * 16);
+        }
+      }
     }
   }
 
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  if (warp == 5) {
+  if (warp == kMma) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
                  "r"(C::kTmemCols)
                  : "memory");
   }
 }
-
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
                                   const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
                                   const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
@@ -513,21 +550,22 @@ cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cuda
   long long tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
   int grid = (int)(tiles < num_sms ? tiles : num_sms);
   count_launch();
-  tc_gemm_kernel<BN, NP><<<grid, 192, C::kSmem, stream>>>(ta, tb, g);
+  tc_gemm_kernel<BN, NP><<<grid, C::kThreads, C::kSmem, stream>>>(ta, tb, g);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 void tc_set_pairs(TcGemm& g, int nplanes) {
+  // Product 0 must be hi * hi: it is accumulated exactly in its own TMEM buffer.
   g.nplanes = nplanes;
   if (nplanes == 2) {
-    const int a[3] = {1, 0, 0}, b[3] = {0, 1, 0};
+    const int a[3] = {0, 1, 0}, b[3] = {0, 0, 1};
     g.npairs = 3;
     for (int i = 0; i < 3; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
   } else {
-    // smallest products first, the hi*hi product last
-    const int a[6] = {2, 1, 0, 1, 0, 0}, b[6] = {0, 1, 2, 0, 1, 0};
+    // the remaining products smallest first
+    const int a[6] = {0, 2, 1, 0, 1, 0}, b[6] = {0, 0, 1, 2, 0, 1};
     g.npairs = 6;
     for (int i = 0; i < 6; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
   }
@@ -537,13 +575,12 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
                     int num_sms) {
   if (g.M <= 0 || g.N <= 0) return cudaSuccess;
   if (A.K != B.K || A.K != g.K || A.K % 8 != 0 || A.rows < g.M || B.rows < g.N ||
-      A.planes != g.nplanes || B.planes != g.nplanes)
+      A.planes != g.nplanes || B.planes != g.nplanes || g.npairs < 1 || g.pa[0] != 0 ||
+      g.pb[0] != 0)
     return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A.ptr) | reinterpret_cast<uintptr_t>(B.ptr)) & 15)
     return cudaErrorInvalidValue;
-  const bool comp = g.kchunk > 0 && g.kchunk < (g.K + BK - 1) / BK;
   if (g.nplanes == 2) {
-    if (!comp && g.N > 128) return launch<256, 2>(A, B, g, stream, num_sms);
     if (g.N > 64) return launch<128, 2>(A, B, g, stream, num_sms);
     return launch<64, 2>(A, B, g, stream, num_sms);
   }

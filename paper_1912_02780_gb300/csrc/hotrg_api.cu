@@ -143,6 +143,7 @@ struct hotrg_plan_s {
   int* err = nullptr;
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
+  float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
   bool have_fwd = false, fwd_ising = false;
   std::string last_error;
   // optional per-stage CUDA-event timing
@@ -252,7 +253,7 @@ TcGemm tcg(const hotrg_plan p, int M, int N, int K, IMap cm, IMap cn, int mode, 
   memset(&g, 0, sizeof(g));
   tc_set_pairs(g, p->L.np);
   g.M = M; g.N = N; g.K = K;
-  g.kchunk = (p->L.np == 3) ? 1 : 4;
+  g.kchunk = kGridSeg / 64;   // accumulation chunk = grid segment of the operand split
   g.cm = cm; g.cn = cn;
   g.out_mode = mode;
   g.out_planes = p->L.np;
@@ -267,10 +268,15 @@ TcGemm tcg(const hotrg_plan p, int M, int N, int K, IMap cm, IMap cn, int mode, 
   return g;
 }
 
+// Operand preparation: grid-aligned bf16 planes (see kernels.cu: grid_split).
 cudaError_t gsplit(const hotrg_plan p, const double* src, IMap rm, IMap km, int rows, int K,
                    int np, long long stride, __nv_bfloat16* dst) {
-  return gather_split(src, lim_of(p, src, sizeof(double)), rm, km, rows, K, np, stride, dst, p->err,
-                      p->stream, p->sms);
+  return grid_split(src, lim_of(p, src, sizeof(double)), rm, km, rows, K, np, stride, dst, p->err,
+                    p->stream, p->sms);
+}
+cudaError_t fsplit(const hotrg_plan p, int rows, int K, long long stride, __nv_bfloat16* dst) {
+  return grid_split(p->F32, lim_of(p, p->F32, sizeof(float)), map_lin(K), map_lin(1), rows, K,
+                    p->L.np, stride, dst, p->err, p->stream, p->sms);
 }
 
 TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long stride) {
@@ -316,10 +322,12 @@ hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double
   }
   Stage sc(p, kStGram);
   TcOperand ta = opnd(p->pTA, X * Y, X * Y, np, sT), tb = opnd(p->pTB, X * Y, X * Y, np, sT);
-  CK(tc_gemm(ta, ta, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutSplit, p->pA, sG),
+  CK(tc_gemm(ta, ta, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutF32, p->F32, 0),
              st, p->sms));
-  CK(tc_gemm(tb, tb, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutSplit, p->pB, sG),
+  CK(fsplit(p, X * X, Y * Y, sG, p->pA));
+  CK(tc_gemm(tb, tb, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutF32, p->F32, 0),
              st, p->sms));
+  CK(fsplit(p, X * X, Y * Y, sG, p->pB));
   TcOperand a = opnd(p->pA, X * X, Y * Y, np, sG), b = opnd(p->pB, X * X, Y * Y, np, sG);
   CK(tc_gemm(a, b, tcg(p, X * X, X * X, Y * Y, map2(X, X, (long long)X * X * X),
                        map2(X, 1, (long long)X * X), kOutF64, G, 0),
@@ -385,16 +393,21 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     Stage sc(p, kStS1);
     CK(tc_gemm(w1, t1,
                tcg(p, Xp * X, yc * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
-                   kOutSplit, p->pU, sC),
+                   kOutF32, p->F32, 0),
                st, p->sms));
+    CK(fsplit(p, yc * X * Xp, X * Y, sC, p->pU));
     }
     const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
     {
     Stage sc(p, kStS2);
     CK(tc_gemm(u, pp,
                tcg(p, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
-                   map2(X, 1, X2), kOutSplit, p->pV, sC),
+                   map2(X, 1, X2), kOutF32, p->F32, 0),
                st, p->sms));
+    }
+    {
+    Stage sc(p, kStPrep);
+    CK(fsplit(p, yc * Xp * Y, X * X, sC, p->pV));
     }
     const TcOperand v = opnd(p->pV, yc * Xp * Y, X * X, np, sC);
     Stage sc(p, kStS3);
@@ -667,6 +680,7 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
     b.add(L.splitG * L.np, 2 * 2);
     b.add((L.splitW1 + L.splitW3) * L.np, 2);
     b.add(L.chunkS * L.np, 2 * 2);
+    b.add(L.chunkS > L.splitG ? L.chunkS : L.splitG, 4);
   }
   b.total += (size_t)64 << 20;  // solver workspace and small buffers (estimate)
   *bytes = b.total;
@@ -757,6 +771,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     ALC(p->pW3, L.splitW3 * np);
     ALC(p->pU, L.chunkS * np);
     ALC(p->pV, L.chunkS * np);
+    ALC(p->F32, L.chunkS > L.splitG ? L.chunkS : L.splitG);
   }
   if (cusolverDnCreate(&p->solver) != CUSOLVER_STATUS_SUCCESS) return cleanup(HOTRG_ECUDA);
   if (cusolverDnSetStream(p->solver, p->stream) != CUSOLVER_STATUS_SUCCESS)
@@ -960,8 +975,8 @@ hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk,
   cudaMemcpy(dA, A, sizeof(double) * M * (size_t)K, cudaMemcpyHostToDevice);
   cudaMemcpy(dB, B, sizeof(double) * N * (size_t)K, cudaMemcpyHostToDevice);
   cudaMemset(err, 0, sizeof(int));
-  gather_split(dA, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, 0, sms);
-  gather_split(dB, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, 0, sms);
+  grid_split(dA, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, 0, sms);
+  grid_split(dB, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, 0, sms);
   tc_set_pairs(g, planes);
   g.M = M; g.N = N; g.K = K; g.kchunk = kchunk;
   g.cm = map_lin(N); g.cn = map_lin(1);

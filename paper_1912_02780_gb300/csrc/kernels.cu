@@ -41,6 +41,84 @@ __global__ void gather_split_kernel(const double* __restrict__ src, long long sr
   }
 }
 
+// Grid-aligned split for the tensor-core GEMM.  One warp per (row, K segment
+// of `seg` <= 128 elements).  With three planes, plane 0 is the value rounded
+// to the grid g = 2^(e-8), 2^(e-1) <= max|segment| < 2^e, so |plane0 / g| <= 256
+// is an integer that bf16 holds exactly; planes 1 and 2 are the bf16
+// round-to-nearest of the remainders.  With every operand split this way, the
+// products of the two plane-0 values of a segment are integers on the grid
+// g_a g_b below 2^16, and their sum over a segment of 128 stays below 2^23:
+// the FP32 tensor-core accumulation of those products is exact.  With two
+// planes, plane 0 is the plain round-to-nearest bf16 of the value (a grid
+// would cost the remainder plane bits on small elements).
+template <typename SrcT>
+__global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm,
+                                  IMap km, int rows, int K, int seg, int nplanes, int gridded,
+                                  long long plane_stride, __nv_bfloat16* __restrict__ dst,
+                                  int* err) {
+  const int lane = threadIdx.x & 31;
+  const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
+  const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const int nseg = (K + seg - 1) / seg;
+  const long long work = (long long)rows * nseg;
+  for (long long w = warp0; w < work; w += nwarps) {
+    const int r = (int)(w / nseg), sg = (int)(w % nseg);
+    const int k0 = sg * seg;
+    const long long roff = imap(rm, r);
+    float v[4];
+    double vd[4];
+    float mx = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int kk = lane + 32 * i;
+      const int k = k0 + kk;
+      vd[i] = 0.0;
+      if (kk < seg && k < K) {
+        const long long off = roff + imap(km, k);
+        if (off >= 0 && off < src_lim) vd[i] = (double)src[off];
+        else atomicOr(err, kErrBounds);
+      }
+      v[i] = (float)vd[i];
+      mx = fmaxf(mx, fabsf(v[i]));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    // grid 2^(e-8) with 2^(e-1) <= max < 2^e, kept a normal float (tiny segments
+    // get a coarser grid, which keeps the plane-0 integers even smaller)
+    int e = 0;
+    frexpf(mx, &e);
+    const float g = (mx > 0.f) ? ldexpf(1.f, max(e - 8, -126)) : 1.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const int kk = lane + 32 * i;
+      const int k = k0 + kk;
+      if (kk < seg && k < K) {
+        const long long o = (long long)r * K + k;
+        __nv_bfloat16 b0;
+        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
+        else b0 = __double2bfloat16(vd[i]);
+        dst[o] = b0;
+        if (nplanes > 1) {
+          __nv_bfloat16 b1, b2;
+          if constexpr (sizeof(SrcT) == 4) {
+            // float source: the remainders are exact in float
+            const float rem = v[i] - __bfloat162float(b0);
+            b1 = __float2bfloat16_rn(rem);
+            b2 = __float2bfloat16_rn(rem - __bfloat162float(b1));
+          } else {
+            // double source: keep the bits a float would drop
+            const double rem = vd[i] - (double)__bfloat162float(b0);
+            b1 = __double2bfloat16(rem);
+            b2 = __double2bfloat16(rem - (double)__bfloat162float(b1));
+          }
+          dst[plane_stride + o] = b1;
+          if (nplanes > 2) dst[2 * plane_stride + o] = b2;
+        }
+      }
+    }
+  }
+}
+
 // T0 and dT0/dbeta of the Ising model (one tensor per spin).
 __global__ void ising_t0_kernel(double beta, double J, double h, double* T0, double* dT0) {
   int idx = threadIdx.x;   // 16 threads: (l, r, u, d) bits
@@ -288,6 +366,39 @@ cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km,
   gather_split_kernel<<<blocks_for(n, sms), 256, 0, st>>>(src, src_lim, rm, km, rows, K, nplanes,
                                                           plane_stride, dst, err);
   return cudaGetLastError();
+}
+
+template <typename SrcT>
+cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                         int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                         cudaStream_t st, int sms) {
+  // Plane 0 on the grid only for three planes; with two planes a floating
+  // plane 0 keeps more bits for small elements (see the comment above).
+  const int gridded = nplanes >= 3 ? 1 : 0;
+  const int seg = K < kGridSeg ? K : kGridSeg;
+  const long long work = (long long)rows * ((K + seg - 1) / seg);
+  if (work == 0) return cudaSuccess;
+  if ((long long)rows * K > plane_stride) return cudaErrorInvalidValue;
+  long long blocks = (work + 7) / 8;   // 8 warps per block
+  if (blocks > 32LL * sms) blocks = 32LL * sms;
+  count_launch();
+  grid_split_kernel<SrcT><<<(int)blocks, 256, 0, st>>>(src, src_lim, rm, km, rows, K, seg, nplanes,
+                                                        gridded, plane_stride, dst, err);
+  return cudaGetLastError();
+}
+
+cudaError_t grid_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                       int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                       cudaStream_t st, int sms) {
+  return grid_split_t<double>(src, src_lim, rm, km, rows, K, nplanes, plane_stride, dst, err, st,
+                              sms);
+}
+
+cudaError_t grid_split(const float* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                       int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                       cudaStream_t st, int sms) {
+  return grid_split_t<float>(src, src_lim, rm, km, rows, K, nplanes, plane_stride, dst, err, st,
+                             sms);
 }
 
 cudaError_t ising_t0(double beta, double J, double h, double* T0, double* dT0, cudaStream_t st) {

@@ -9,6 +9,15 @@ namespace hotrg {
 cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
                          int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
                          cudaStream_t st, int sms);
+// Grid-aligned bf16 split (segments of kGridSeg along K, see kernels.cu):
+// the operand preparation the tensor-core GEMM's exact hi*hi accumulation needs.
+constexpr int kGridSeg = 128;
+cudaError_t grid_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                       int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                       cudaStream_t st, int sms);
+cudaError_t grid_split(const float* src, long long src_lim, IMap rm, IMap km, int rows, int K,
+                       int nplanes, long long plane_stride, __nv_bfloat16* dst, int* err,
+                       cudaStream_t st, int sms);
 cudaError_t ising_t0(double beta, double J, double h, double* T0, double* dT0, cudaStream_t st);
 // x <- x / ||x||_F (FP64, deterministic), *log_norm = ln ||x||_F.
 cudaError_t frob_normalize(double* x, long long n, double* partial, int max_partial,
