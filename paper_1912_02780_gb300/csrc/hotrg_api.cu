@@ -467,8 +467,31 @@ hotrg_status run_forward(hotrg_plan p) {
 
 // ---- backward pieces ------------------------------------------------------
 
-hotrg_status step_backward_f64(hotrg_plan p, int k) {
+// One contraction of the backward: on the tensor cores (grid-aligned split of
+// both operands from their FP64 sources through the same index maps, FP64
+// output, optional accumulation) when the step runs split and the operands fit
+// the plane buffers, else on the FP64 GEMM.
+cudaError_t run_gemm(hotrg_plan p, bool split, const GemmF64& g) {
+  const long long cap = p->L.chunkS;
+  const bool ok = split && p->L.any_split && g.K % 8 == 0 && (g.beta == 0.0 || g.beta == 1.0) &&
+                  (long long)g.M * g.K <= cap && (long long)g.N * g.K <= cap && g.K > 0;
+  if (!ok) return gemm_f64(g, p->stream, p->sms);
+  const int np = p->L.np;
+  cudaError_t e = grid_split(g.A, g.a_lim, g.am, g.ak, g.M, g.K, np, cap, p->pU, p->err,
+                             p->stream, p->sms);
+  if (e != cudaSuccess) return e;
+  e = grid_split(g.B, g.b_lim, g.bn, g.bk, g.N, g.K, np, cap, p->pV, p->err, p->stream, p->sms);
+  if (e != cudaSuccess) return e;
+  TcGemm t = tcg(p, g.M, g.N, g.K, g.cm, g.cn, kOutF64, g.C, 0);
+  t.alpha = (float)g.alpha;
+  t.accumulate = g.beta != 0.0 ? 1 : 0;
+  return tc_gemm(opnd(p->pU, g.M, g.K, np, cap), opnd(p->pV, g.N, g.K, np, cap), t, p->stream,
+                 p->sms);
+}
+
+hotrg_status step_backward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
+  const bool sp = s.split;
   const int X = s.X, Y = s.Y, Xp = s.Xp;
   const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
   const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X, YXp2 = (long long)Y * Xp2;
@@ -481,53 +504,45 @@ hotrg_status step_backward_f64(hotrg_plan p, int k) {
   CK(cudaMemsetAsync(p->Tbar, 0, sizeof(double) * X2 * Y2, st));
   CK(cudaMemsetAsync(p->wbT, 0, sizeof(double) * Xp * N, st));
   {
-  Stage sc(p, kStBwdContract + kStF64);
+  Stage sc(p, kStBwdContract + (sp ? 0 : kStF64));
   for (int y0 = 0; y0 < Y; y0 += s.yc64) {
     const int yc = (Y - y0) < s.yc64 ? (Y - y0) : s.yc64;
     const double* Ty = T + (long long)y0 * Y;
     const double* Eby = Eb + (long long)y0 * YXp2;
     // recompute U and V of this chunk (as in the forward)
-    CK(gemm_f64(g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
+    CK(run_gemm(p, sp, g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
                     map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY), Xp * X, yc * X * Y, X,
-                    1.0, 0.0),
-                st, p->sms));
-    CK(gemm_f64(g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
+                    1.0, 0.0)));
+    CK(run_gemm(p, sp, g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
                     map3(Xp, X, Y * X2, X, Xp * Y * X2), map2(X, 1, X2), yc * X * Xp, Y * X,
-                    X * Y, 1.0, 0.0),
-                st, p->sms));
+                    X * Y, 1.0, 0.0)));
     // P[(y a i)][(k z)] = sum_b Tbar'[a b y z] w[i k b]
-    CK(gemm_f64(g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
+    CK(run_gemm(p, sp, g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
                     p->Pb, map3(Y, Xp, 1, X2 * Y, (long long)Xp * X2 * Y), map2(X, Y, XY),
-                    yc * Xp * Y, X * X, Xp, 1.0, 0.0),
-                st, p->sms));
+                    yc * Xp * Y, X * X, Xp, 1.0, 0.0)));
     // Q[(y a i)][(b j)] = sum_{k z} P T[b k j z]
-    CK(gemm_f64(g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
-                    map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0),
-                st, p->sms));
+    CK(run_gemm(p, sp, g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
+                    map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0)));
     // upper copy: Tbar[a i y j] += sum_{A b} w[a b A] Q[y A i b j]
-    CK(gemm_f64(g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
+    CK(run_gemm(p, sp, g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
                     map2(X, Y, X * XY), p->Tbar + (long long)y0 * Y, map_lin(XY2),
-                    map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0),
-                st, p->sms));
+                    map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0)));
     // lower copy: Tbar[b k j z] += sum_{y i A} U[y i A b j] P[y A z i k]
-    CK(gemm_f64(g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
+    CK(run_gemm(p, sp, g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
                     map2(Y, 1, Y), map3(Xp, X, X * XY, XY, (long long)Xp * X * XY), p->Tbar,
-                    map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0),
-                st, p->sms));
+                    map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0)));
     // w carrying alpha: wbT[A][(a b)] += sum_{y i j} T[a i y j] Q[y A i b j]
-    CK(gemm_f64(g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
+    CK(run_gemm(p, sp, g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
                     map3(Y, X, 1, XY, (long long)Xp * X * XY), p->wbT, map_lin(X), map2(X, 1, N),
-                    X, Xp * X, yc * X * Y, 1.0, 1.0),
-                st, p->sms));
+                    X, Xp * X, yc * X * Y, 1.0, 1.0)));
     // w carrying beta: wbT[B][(i k)] += sum_{y A z} V[y A z][(i k)] Tbar'[A B y z]
-    CK(gemm_f64(g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
+    CK(run_gemm(p, sp, g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
                     map_lin(1), map3(Y, Xp, Xp2, Xp, YXp2), p->wbT, map_lin(1), map_lin(N),
-                    X * X, Xp, yc * Xp * Y, 1.0, 1.0),
-                st, p->sms));
+                    X * X, Xp, yc * Xp * Y, 1.0, 1.0)));
   }
   }
   if (!p->cfg.fixed_w_grad && Xp < N) {
-    Stage sc(p, kStBwdEigh + kStF64);
+    Stage sc(p, kStBwdEigh + (sp ? 0 : kStF64));
     const int nd = (int)(N - Xp);
     const double* Ud = Ek + (long long)Xp * N;
     // S[j][k] = sum_i U_d[i][j] wbar[i][k]
@@ -544,26 +559,30 @@ hotrg_status step_backward_f64(hotrg_plan p, int k) {
                     map_lin(N), map_lin(1), (int)N, (int)N, Xp, 1.0, 0.0),
                 st, p->sms));
     CK(symmetrize(p->Gb, (int)N, st, p->sms));
-    hotrg_status r = gram_f64(p, s, T, p->Abuf, p->Bbuf, nullptr);
-    if (r != HOTRG_OK) return r;
+    {
+      // Gram halves again (A, B of the forward), FP64 output
+      const long long XY2g = (long long)X * Y * Y, Y2g = (long long)Y * Y;
+      CK(run_gemm(p, sp, g64(p, T, map2(Y, 1, XY2g), map2(Y, Y, Y2g), T, map2(Y, 1, XY2g),
+                             map2(Y, Y, Y2g), p->Abuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
+                             X * Y, X * Y, 1.0, 0.0)));
+      CK(run_gemm(p, sp, g64(p, T, map2(Y, Y, XY2g), map2(Y, 1, Y2g), T, map2(Y, Y, XY2g),
+                             map2(Y, 1, Y2g), p->Bbuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
+                             X * Y, X * Y, 1.0, 0.0)));
+    }
     const long long X3 = X2 * X;
     // Abar[(x1 x1'')][(j j')] = sum_{x2 x2''} Gbar[x1 x2 x1'' x2''] B[(x2 x2'')][(j j')]
-    CK(gemm_f64(g64(p, p->Gb, map2(X, X, X3), map2(X, 1, X2), p->Bbuf, map_lin(1), map_lin(Y2),
-                    p->Abar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0),
-                st, p->sms));
-    CK(gemm_f64(g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
-                    p->Bbar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0),
-                st, p->sms));
+    CK(run_gemm(p, sp, g64(p, p->Gb, map2(X, X, X3), map2(X, 1, X2), p->Bbuf, map_lin(1), map_lin(Y2),
+                    p->Abar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
+    CK(run_gemm(p, sp, g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
+                    p->Bbar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
     // Tbar[a i y j] += 2 sum_{c k} Abar[a j c k] T[c i y k]
-    CK(gemm_f64(g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
+    CK(run_gemm(p, sp, g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
                     map2(Y, 1, XY2), p->Tbar, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, X * Y,
-                    2.0, 1.0),
-                st, p->sms));
+                    2.0, 1.0)));
     // Tbar[b k j z] += 2 sum_{d m} Bbar[b j d m] T[d k m z]
-    CK(gemm_f64(g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
+    CK(run_gemm(p, sp, g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
                     map2(Y, Y, XY2), p->Tbar, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y,
-                    2.0, 1.0),
-                st, p->sms));
+                    2.0, 1.0)));
   }
   // E_{k-1} = (1/2) Tbar (average of the two copies), in the layout of T_{k-1}
   CK(scale_copy(p->Tbar, p->Enext, X2 * Y2, 0.5, st, p->sms));
@@ -577,7 +596,7 @@ hotrg_status run_backward(hotrg_plan p) {
   const StepGeom& last = p->L.g.back();
   CK(seed_trace_adjoint(p->Ecur, last.Y, last.Xp, p->scal + 1, p->stream, p->sms));
   for (int k = p->cfg.n_steps; k >= 1; --k) {
-    hotrg_status r = step_backward_f64(p, k);
+    hotrg_status r = step_backward(p, k);
     if (r != HOTRG_OK) return r;
   }
   return HOTRG_OK;

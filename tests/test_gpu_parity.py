@@ -134,3 +134,32 @@ def test_forward_split_c4_d64_against_stored_oracle():
     assert sign == g["trace_sign"]
     assert np.max(np.abs(ln[:4] - np.array(g["log_norms"][:4]))) < 1e-12   # FP64 steps
     assert err < 1e-8
+
+
+@pytest.mark.parametrize("precision", ["bf16x6", "fp64"])
+@pytest.mark.parametrize("d_cut,n", [(16, 10), (32, 9)])
+def test_backward_split_random_tensor(precision, d_cut, n):
+    """Backward with the contractions on the tensor cores (split from step 3)
+    against the oracle's full gradient; ~1e-6 relative is the target."""
+    T0 = synth.random_symmetric_T0(2, 4)
+    f = hotrg.hotrg_forward(T0, d_cut, n)
+    g_ref = hotrg.hotrg_backward(f)
+    with hot.Plan(4, d_cut, n, precision, split_from_step=3) as p:
+        p.forward_tensor(T0)
+        g = p.backward()
+    err = np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))
+    print(f"{precision} D={d_cut}: grad rel err = {err:.3e}, euler = {np.sum(g * T0) - 1:.2e}")
+    assert err < (5e-6 if precision == "bf16x6" else 1e-9)
+    assert abs(np.sum(g * T0) - 1.0) < 1e-6
+
+
+def test_backward_split_ising_dbeta():
+    beta, d_cut, n = 0.44, 16, 14
+    f = hotrg.hotrg_forward(ising.ising_T0(beta), d_cut, n)
+    g_ref = hotrg.hotrg_backward(f)
+    db_ref = float(np.sum(g_ref * ising.ising_dT0_dbeta(beta)))
+    with hot.Plan(2, d_cut, n, "bf16x6", split_from_step=5) as p:
+        lnz, _, _ = p.forward_ising(beta, 1.0, 0.0)
+        g, db = p.backward(want_dbeta=True)
+    print(f"ising split: |dlnz| = {abs(lnz - f['lnz']):.2e}, dbeta rel err = {abs(db - db_ref) / abs(db_ref):.2e}")
+    assert abs(db - db_ref) / abs(db_ref) < 1e-6
