@@ -188,6 +188,41 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args):
+    """Continuous-batching serving run: seeded Poisson arrivals of Ising solves
+    (beta ~ U[0.30, 0.60], h ~ U[0, 0.05], D_cut in {16, 24, 32, 48, 64},
+    n_steps in [20, 40], half of them with gradients), replayed in real time
+    into the solve server; latency = finish - submit on the server's clock."""
+    import paper_1912_02780_gb300 as hot
+    stream = synth.serving_stream(seed=2024, n=args.requests, rate=args.rate)
+    srv = hot.Server(int(args.budget_gb * 2 ** 30), args.slots)
+    t0 = time.perf_counter()
+    tickets = []
+    for r in stream:
+        dt = r["t_arrival"] - (time.perf_counter() - t0)
+        if dt > 0:
+            time.sleep(dt)
+        tickets.append(srv.submit(r["beta"], r["J"], r["h"], r["d_cut"], r["n_steps"],
+                                  r["want_grad"], args.precision, args.split_from))
+    res = [srv.wait(t) for t in tickets]
+    st = srv.stats()
+    srv.close()
+    lat = np.array([x.t_finish - x.t_submit for x in res])
+    svc = np.array([x.t_finish - x.t_start for x in res])
+    span = max(x.t_finish for x in res) - min(x.t_submit for x in res)
+    ok = sum(1 for x in res if x.status == 0)
+    line = {"metric": "serving latency p50/p99 (s)", "value": float(np.percentile(lat, 50)),
+            "p99": float(np.percentile(lat, 99)), "unit": "s", "higher_is_better": False,
+            "solves_per_s": ok / span, "offered_rate": args.rate,
+            "achieved_rate": ok / span, "requests": len(res), "ok": ok,
+            "service_time_mean_s": float(svc.mean()), "slots": args.slots,
+            "budget_gb": args.budget_gb, "peak_gb": st["peak_bytes"] / 2 ** 30,
+            "plans_created": st["plans_created"], "plans_evicted": st["plans_evicted"],
+            "precision": args.precision, "split_from_step": args.split_from,
+            "data": "synthetic", "config": {"workload": "ising serving stream", "seed": 2024}}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -200,7 +235,15 @@ def main():
     ap.add_argument("--grad", type=int, default=0, help="1: each step is forward + backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--serve", action="store_true",
+                    help="serving benchmark: Poisson stream of Ising solves through the server")
+    ap.add_argument("--requests", type=int, default=64)
+    ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
+    ap.add_argument("--slots", type=int, default=4)
+    ap.add_argument("--budget-gb", type=float, default=160.0)
     args = ap.parse_args()
+    if args.serve:
+        return run_serve(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -58,7 +58,8 @@ typedef enum {
   HOTRG_ENONFINITE = 5,   /* a norm or the final trace was zero, NaN or infinite   */
   HOTRG_ETIMEOUT = 6,     /* a bounded device-side wait gave up (error word set)   */
   HOTRG_ESTATE = 7,       /* call out of order (backward before a forward)         */
-  HOTRG_EUNSUPPORTED = 8  /* option not available on this device or build          */
+  HOTRG_EUNSUPPORTED = 8, /* option not available on this device or build          */
+  HOTRG_EPENDING = 9      /* server: the request has not finished yet              */
 } hotrg_status;
 
 typedef enum {
@@ -146,6 +147,48 @@ const char* hotrg_last_error(hotrg_plan plan);
 /* Device capability check: HOTRG_OK if the current device can run the split
  * tensor-core path (compute capability 10.3). */
 hotrg_status hotrg_device_supports_split(void);
+
+/* ---- Solve server (continuous batching) -------------------------------------
+ * Ising solves (forward, optionally backward) submitted at any time are run by
+ * max_slots concurrent slots, each a host worker thread with its own CUDA
+ * stream on the device current at hotrg_server_create, so requests that arrive
+ * while others are on the GPU start as soon as a slot and device memory are
+ * free and their kernels overlap on the device.  Every live plan is charged
+ * its hotrg_plan_workspace_bytes against hbm_budget_bytes; slots keep built
+ * plans for reuse by later requests of the same shape and free idle ones when
+ * a new plan would not fit.  A request whose plan alone exceeds the budget
+ * finishes with status HOTRG_ENOMEM.  Times are seconds since the server was
+ * created.  Submit, poll, wait, drain and stats are thread-safe. */
+typedef struct hotrg_server_s* hotrg_server;
+typedef struct {
+  double beta, J, h;        /* Ising parameters (beta * J >= 0)                     */
+  int d_cut, n_steps;       /* truncation and number of steps                       */
+  int want_grad;            /* 1: also run the backward and return d(lnZ/N)/d beta  */
+  int precision;            /* hotrg_precision of the split steps                   */
+  int split_from_step;      /* as in hotrg_config                                   */
+} hotrg_request;
+typedef struct {
+  uint64_t ticket;
+  int status;               /* hotrg_status of the solve                            */
+  int slot;                 /* slot that ran it                                     */
+  double lnz_per_site, dlnz_dbeta;
+  double t_submit, t_start, t_finish;
+} hotrg_result;
+typedef struct {
+  uint64_t submitted, completed, failed, plans_created, plans_evicted;
+  size_t bytes_in_use, peak_bytes;
+  int queue_depth, busy_slots;
+} hotrg_server_stats;
+hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_server* out);
+hotrg_status hotrg_server_submit(hotrg_server server, const hotrg_request* req, uint64_t* ticket);
+/* HOTRG_EPENDING until the request has finished; then the result (kept until destroy). */
+hotrg_status hotrg_server_poll(hotrg_server server, uint64_t ticket, hotrg_result* out);
+hotrg_status hotrg_server_wait(hotrg_server server, uint64_t ticket, hotrg_result* out);
+/* Block until the queue is empty and no slot is running. */
+hotrg_status hotrg_server_drain(hotrg_server server);
+hotrg_status hotrg_server_get_stats(hotrg_server server, hotrg_server_stats* out);
+/* Finishes every queued request, then frees all plans and joins the slots. */
+void hotrg_server_destroy(hotrg_server server);
 
 /* Per-stage timing.  hotrg_profile_enable(plan, 1) creates a pool of CUDA
  * events (outside any forward/backward) and from then on brackets every stage

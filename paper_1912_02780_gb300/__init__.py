@@ -23,7 +23,7 @@ PRECISIONS = {"fp64": FP64, "bf16x3": BF16X3, "bf16x6": BF16X6}
 
 STATUS = {0: "HOTRG_OK", 1: "HOTRG_EINVAL", 2: "HOTRG_ENOMEM", 3: "HOTRG_ECUDA",
           4: "HOTRG_ENOTCONV", 5: "HOTRG_ENONFINITE", 6: "HOTRG_ETIMEOUT",
-          7: "HOTRG_ESTATE", 8: "HOTRG_EUNSUPPORTED"}
+          7: "HOTRG_ESTATE", 8: "HOTRG_EUNSUPPORTED", 9: "HOTRG_EPENDING"}
 
 # Every symbol declared in include/hotrg.h.
 EXPORTS = (
@@ -34,6 +34,8 @@ EXPORTS = (
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
     "hotrg_gemm_split_noalloc",
+    "hotrg_server_create", "hotrg_server_submit", "hotrg_server_poll", "hotrg_server_wait",
+    "hotrg_server_drain", "hotrg_server_get_stats", "hotrg_server_destroy",
 )
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
@@ -45,6 +47,27 @@ class hotrg_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("split_from_step", ctypes.c_int),
                 ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
                 ("eigh_broadening", ctypes.c_double)]
+
+
+class hotrg_request(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("J", ctypes.c_double), ("h", ctypes.c_double),
+                ("d_cut", ctypes.c_int), ("n_steps", ctypes.c_int), ("want_grad", ctypes.c_int),
+                ("precision", ctypes.c_int), ("split_from_step", ctypes.c_int)]
+
+
+class hotrg_result(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("status", ctypes.c_int), ("slot", ctypes.c_int),
+                ("lnz_per_site", ctypes.c_double), ("dlnz_dbeta", ctypes.c_double),
+                ("t_submit", ctypes.c_double), ("t_start", ctypes.c_double),
+                ("t_finish", ctypes.c_double)]
+
+
+class hotrg_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_uint64), ("completed", ctypes.c_uint64),
+                ("failed", ctypes.c_uint64), ("plans_created", ctypes.c_uint64),
+                ("plans_evicted", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
+                ("peak_bytes", ctypes.c_size_t), ("queue_depth", ctypes.c_int),
+                ("busy_slots", ctypes.c_int)]
 
 
 class HotrgError(RuntimeError):
@@ -94,9 +117,17 @@ def lib() -> ctypes.CDLL:
     L.hotrg_kernel_launches.argtypes = []
     L.hotrg_kernel_launches.restype = ctypes.c_ulonglong
     L.hotrg_gemm_split_noalloc.argtypes = [ctypes.c_int] * 5 + [vp, vp, vp, vp]
+    L.hotrg_server_create.argtypes = [ctypes.c_size_t, ctypes.c_int, ctypes.POINTER(vp)]
+    L.hotrg_server_submit.argtypes = [vp, ctypes.POINTER(hotrg_request), ctypes.POINTER(ctypes.c_uint64)]
+    L.hotrg_server_poll.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hotrg_result)]
+    L.hotrg_server_wait.argtypes = [vp, ctypes.c_uint64, ctypes.POINTER(hotrg_result)]
+    L.hotrg_server_drain.argtypes = [vp]
+    L.hotrg_server_get_stats.argtypes = [vp, ctypes.POINTER(hotrg_server_stats)]
+    L.hotrg_server_destroy.argtypes = [vp]
+    L.hotrg_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
-                        "hotrg_last_error", "hotrg_kernel_launches"):
+                        "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy"):
             getattr(L, name).restype = ctypes.c_int
     _LIB = L
     return L
@@ -227,6 +258,65 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Server:
+    """Continuous-batching solve server (see include/hotrg.h)."""
+
+    def __init__(self, hbm_budget_bytes: int, max_slots: int = 4):
+        h = ctypes.c_void_p(0)
+        s = lib().hotrg_server_create(int(hbm_budget_bytes), int(max_slots), ctypes.byref(h))
+        if s:
+            raise HotrgError(s, "hotrg_server_create")
+        self._h = h
+
+    def submit(self, beta, J=1.0, h=0.0, d_cut=16, n_steps=20, want_grad=False, precision="fp64",
+               split_from_step=1) -> int:
+        r = hotrg_request(beta, J, h, d_cut, n_steps, int(bool(want_grad)),
+                          PRECISIONS[precision] if isinstance(precision, str) else int(precision),
+                          split_from_step)
+        t = ctypes.c_uint64(0)
+        s = lib().hotrg_server_submit(self._h, ctypes.byref(r), ctypes.byref(t))
+        if s:
+            raise HotrgError(s, "submit")
+        return t.value
+
+    def poll(self, ticket: int):
+        r = hotrg_result()
+        s = lib().hotrg_server_poll(self._h, ticket, ctypes.byref(r))
+        if s == 9:
+            return None
+        if s:
+            raise HotrgError(s, "poll")
+        return r
+
+    def wait(self, ticket: int) -> hotrg_result:
+        r = hotrg_result()
+        s = lib().hotrg_server_wait(self._h, ticket, ctypes.byref(r))
+        if s:
+            raise HotrgError(s, "wait")
+        return r
+
+    def drain(self):
+        s = lib().hotrg_server_drain(self._h)
+        if s:
+            raise HotrgError(s, "drain")
+
+    def stats(self) -> dict:
+        st = hotrg_server_stats()
+        lib().hotrg_server_get_stats(self._h, ctypes.byref(st))
+        return {f: getattr(st, f) for f, _ in st._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().hotrg_server_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
 
     def __enter__(self):
         return self

@@ -97,12 +97,32 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmF64 p, int k_per_spli
       }
       double* c = p.C + off;
       double v = p.alpha * acc[i][j];
-      if (gridDim.z > 1) {
+      if (gridDim.z > 1 && p.ws) {
+        p.ws[((long long)blockIdx.z * p.M + m) * p.N + n] = acc[i][j];
+      } else if (gridDim.z > 1) {
         atomicAdd(c, v);
       } else {
         *c = (p.beta != 0.0) ? v + p.beta * *c : v;
       }
     }
+  }
+}
+
+// Fixed-order sum of the split-K partials: C = alpha * sum_z ws[z] + beta * C.
+__global__ void splitk_reduce_kernel(GemmF64 p, int splits) {
+  long long total = (long long)p.M * p.N;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    int m = (int)(i / p.N), n = (int)(i % p.N);
+    double s = 0.0;
+    for (int z = 0; z < splits; ++z) s += p.ws[(long long)z * total + i];
+    const long long off = imap(p.cm, m) + imap(p.cn, n);
+    if (off < 0 || off >= p.c_lim) {
+      atomicOr(p.err, kErrBounds);
+      continue;
+    }
+    double* c = p.C + off;
+    *c = (p.beta != 0.0) ? p.alpha * s + p.beta * *c : p.alpha * s;
   }
 }
 
@@ -142,14 +162,15 @@ cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms) {
     k_per_split = ((p.K + splits - 1) / splits + BK - 1) / BK * BK;
     splits = (p.K + k_per_split - 1) / k_per_split;
   }
-  if (splits > 1) {
+  const bool det = splits > 1 && p.ws && (long long)splits * p.M * p.N <= p.ws_elems;
+  if (splits > 1 && !det) {
     long long total = (long long)p.M * p.N;
     int blocks = (int)((total + 255) / 256);
     if (blocks > 8 * num_sms) blocks = 8 * num_sms;
     count_launch();
     scale_out_kernel<<<blocks, 256, 0, stream>>>(p);
-    grid.z = splits;
   }
+  if (splits > 1) grid.z = splits;
   if (p.K <= 0) {
     if (splits == 1) {
       GemmF64 q = p;
@@ -161,8 +182,17 @@ cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms) {
     }
     return cudaGetLastError();
   }
+  GemmF64 q = p;
+  if (!det) q.ws = nullptr;
   count_launch();
-  gemm_f64_kernel<<<grid, 256, 0, stream>>>(p, k_per_split);
+  gemm_f64_kernel<<<grid, 256, 0, stream>>>(q, k_per_split);
+  if (det) {
+    long long total = (long long)p.M * p.N;
+    int blocks = (int)((total + 255) / 256);
+    if (blocks > 8 * num_sms) blocks = 8 * num_sms;
+    count_launch();
+    splitk_reduce_kernel<<<blocks, 256, 0, stream>>>(p, splits);
+  }
   return cudaGetLastError();
 }
 

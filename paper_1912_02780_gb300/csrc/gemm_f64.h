@@ -14,6 +14,8 @@ struct GemmF64 {
   long long a_lim, b_lim, c_lim;  // element counts behind A, B, C: accesses at or beyond
                                   // them are skipped and flagged (kErrBounds)
   int* err;
+  double* ws;                     // optional split-K workspace: with it, split-K partials are
+  long long ws_elems;             // summed in a fixed order (deterministic); without, atomics
 };
 
 cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms);

@@ -40,6 +40,7 @@ namespace {
 constexpr long long kChunkF64 = 1LL << 27;     // FP64 stage chunk budget (elements)
 constexpr long long kChunkSplit = 1LL << 30;   // split stage chunk budget (elements per plane)
 constexpr int kMaxPartial = 4096;
+constexpr long long kSplitK = 1LL << 25;       // FP64 split-K workspace (elements)
 
 struct StepGeom {
   int X, Y, Xp;
@@ -144,6 +145,7 @@ struct hotrg_plan_s {
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
+  double* splitk = nullptr;   // FP64 split-K partials (deterministic reduction)
   bool have_fwd = false, fwd_ising = false;
   std::string last_error;
   // optional per-stage CUDA-event timing
@@ -237,6 +239,8 @@ GemmF64 g64(const hotrg_plan p, const double* A, IMap am, IMap ak, const double*
   g.b_lim = lim_of(p, B, sizeof(double));
   g.c_lim = lim_of(p, C, sizeof(double));
   g.err = p->err;
+  g.ws = p->splitk;
+  g.ws_elems = kSplitK;
   g.A = A; g.am = am; g.ak = ak;
   g.B = B; g.bn = bn; g.bk = bk;
   g.C = C; g.cm = cm; g.cn = cn;
@@ -701,6 +705,7 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
     b.add(L.chunkS * L.np, 2 * 2);
     b.add(L.chunkS > L.splitG ? L.chunkS : L.splitG, 4);
   }
+  b.add(kSplitK, 8);
   b.total += (size_t)64 << 20;  // solver workspace and small buffers (estimate)
   *bytes = b.total;
   return HOTRG_OK;
@@ -769,6 +774,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     ALC(p->Enext, L.maxT);
     ALC(p->Tbar, L.maxT);
   }
+  ALC(p->splitk, kSplitK);
   ALC(p->dT0, 64);
   ALC(p->partial, kMaxPartial);
   ALC(p->scal, 8);
@@ -1042,6 +1048,8 @@ hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const do
     g.M = M; g.N = N; g.K = K; g.alpha = 1.0; g.beta = 0.0; g.a_kfast = 1; g.b_kfast = 1;
     g.a_lim = (long long)M * K; g.b_lim = (long long)N * K; g.c_lim = (long long)M * N;
     g.err = err;
+    g.ws = nullptr;
+    g.ws_elems = 0;
     if (gemm_f64(g, 0, prop.multiProcessorCount) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess)
       status = HOTRG_ECUDA;
     else if (cudaMemcpy(C, dC, sizeof(double) * M * (size_t)N, cudaMemcpyDeviceToHost) != cudaSuccess)

@@ -1,0 +1,285 @@
+// Continuous-batching solve server over the HOTRG plans.
+//
+// Requests (Ising beta, J, h, D_cut, n_steps, want_grad, precision) enter a
+// FIFO queue.  A fixed number of slots, each a host worker thread with its own
+// CUDA stream, take requests as soon as they are free: a request that arrives
+// while others are on the GPU starts when a slot and enough device memory are
+// available, and its kernels run concurrently with the other slots' (one
+// slot's FP64 eigensolve overlaps another's tensor-core contractions).
+//
+// Admission by device memory: every live plan is charged its
+// hotrg_plan_workspace_bytes against the budget.  A slot keeps the plans it
+// has built (LRU) for reuse by later requests of the same shape; before a new
+// plan is built the slot frees its own idle plans, and if that is not enough
+// it asks the other slots to free their idle plans and waits for memory.  A
+// request that could never fit the budget is rejected with HOTRG_ENOMEM.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <list>
+#include <mutex>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/hotrg.h"
+#include <cuda_runtime.h>
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+struct PlanKey {
+  int d_cut, n_steps, want_grad, precision, split_from_step;
+  bool operator==(const PlanKey& o) const {
+    return d_cut == o.d_cut && n_steps == o.n_steps && want_grad == o.want_grad &&
+           precision == o.precision && split_from_step == o.split_from_step;
+  }
+};
+
+struct CachedPlan {
+  PlanKey key;
+  hotrg_plan plan;
+  size_t bytes;
+};
+
+struct Job {
+  uint64_t ticket;
+  hotrg_request req;
+  double t_submit;
+};
+
+}  // namespace
+
+struct hotrg_server_s {
+  size_t budget = 0;
+  int device = 0;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::deque<Job> queue;
+  std::unordered_map<uint64_t, hotrg_result> results;
+  std::vector<std::thread> workers;
+  std::vector<std::list<CachedPlan>> caches;   // per slot, front = most recent
+  std::vector<int> busy;
+  size_t bytes_in_use = 0, peak_bytes = 0;
+  uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, created = 0, evicted = 0;
+  int trim_epoch = 0;
+  int running = 0;
+  bool stop = false;
+  Clock::time_point t0;
+
+  double now() const { return std::chrono::duration<double>(Clock::now() - t0).count(); }
+};
+
+namespace {
+
+void free_plan(hotrg_server_s* s, CachedPlan& cp) {
+  hotrg_plan_destroy(cp.plan);
+  s->bytes_in_use -= cp.bytes;
+  s->evicted += 1;
+}
+
+// Called with the lock held: drop this slot's idle cached plans (LRU first)
+// until `need` more bytes fit, or all are gone.
+void trim_own(hotrg_server_s* s, int slot, size_t need, std::unique_lock<std::mutex>& lk) {
+  auto& c = s->caches[slot];
+  while (!c.empty() && s->bytes_in_use + need > s->budget) {
+    CachedPlan cp = c.back();
+    c.pop_back();
+    lk.unlock();
+    hotrg_plan_destroy(cp.plan);
+    lk.lock();
+    s->bytes_in_use -= cp.bytes;
+    s->evicted += 1;
+  }
+}
+
+void worker(hotrg_server_s* s, int slot) {
+  cudaSetDevice(s->device);
+  cudaStream_t stream = nullptr;
+  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  int seen_trim = 0;
+  std::unique_lock<std::mutex> lk(s->mu);
+  while (true) {
+    // idle: honour trim requests from slots waiting for memory
+    if (seen_trim != s->trim_epoch) {
+      seen_trim = s->trim_epoch;
+      trim_own(s, slot, s->budget + 1, lk);
+      s->cv.notify_all();
+      continue;
+    }
+    if (s->stop && s->queue.empty()) break;
+    if (s->queue.empty()) {
+      s->cv.wait(lk);
+      continue;
+    }
+    Job job = s->queue.front();
+    s->queue.pop_front();
+    s->busy[slot] = 1;
+    s->running += 1;
+    hotrg_result res;
+    memset(&res, 0, sizeof(res));
+    res.ticket = job.ticket;
+    res.t_submit = job.t_submit;
+    res.slot = slot;
+    const hotrg_request& r = job.req;
+    PlanKey key{r.d_cut, r.n_steps, r.want_grad ? 1 : 0, r.precision, r.split_from_step};
+    hotrg_config cfg;
+    hotrg_config_default(&cfg, 2, r.d_cut, r.n_steps);
+    cfg.precision = r.precision;
+    cfg.split_from_step = r.split_from_step > 0 ? r.split_from_step : 1;
+    cfg.want_grad = r.want_grad ? 1 : 0;
+    size_t bytes = 0;
+    hotrg_status st = hotrg_plan_workspace_bytes(&cfg, &bytes);
+    hotrg_plan plan = nullptr;
+    auto& cache = s->caches[slot];
+    for (auto it = cache.begin(); it != cache.end(); ++it) {
+      if (it->key == key) {
+        CachedPlan cp = *it;
+        cache.erase(it);
+        cache.push_front(cp);
+        plan = cp.plan;
+        break;
+      }
+    }
+    if (st == HOTRG_OK && !plan) {
+      if (bytes > s->budget) {
+        st = HOTRG_ENOMEM;
+      } else {
+        trim_own(s, slot, bytes, lk);
+        while (s->bytes_in_use + bytes > s->budget) {
+          // ask idle slots to free their cached plans, then wait for memory
+          s->trim_epoch += 1;
+          seen_trim = s->trim_epoch;
+          s->cv.notify_all();
+          s->cv.wait_for(lk, std::chrono::milliseconds(50));
+          trim_own(s, slot, bytes, lk);
+        }
+        s->bytes_in_use += bytes;
+        s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
+        lk.unlock();
+        st = hotrg_plan_create(&cfg, stream, &plan);
+        lk.lock();
+        if (st == HOTRG_OK) {
+          s->created += 1;
+          cache.push_front(CachedPlan{key, plan, bytes});
+        } else {
+          s->bytes_in_use -= bytes;
+          plan = nullptr;
+        }
+      }
+    }
+    res.t_start = s->now();
+    lk.unlock();
+    if (st == HOTRG_OK) {
+      st = hotrg_forward_ising(plan, r.beta, r.J, r.h, &res.lnz_per_site, nullptr, nullptr);
+      if (st == HOTRG_OK && r.want_grad) st = hotrg_backward(plan, nullptr, &res.dlnz_dbeta);
+    }
+    lk.lock();
+    res.status = st;
+    res.t_finish = s->now();
+    s->results[job.ticket] = res;
+    s->busy[slot] = 0;
+    s->running -= 1;
+    s->completed += 1;
+    if (st != HOTRG_OK) s->failed += 1;
+    s->cv.notify_all();
+  }
+  for (auto& cp : s->caches[slot]) free_plan(s, cp);
+  s->caches[slot].clear();
+  lk.unlock();
+  cudaStreamSynchronize(stream);
+  cudaStreamDestroy(stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_server* out) {
+  if (!out || max_slots < 1 || max_slots > 64 || hbm_budget_bytes == 0) return HOTRG_EINVAL;
+  *out = nullptr;
+  hotrg_server_s* s = new hotrg_server_s();
+  if (cudaGetDevice(&s->device) != cudaSuccess) {
+    delete s;
+    return HOTRG_ECUDA;
+  }
+  s->budget = hbm_budget_bytes;
+  s->t0 = Clock::now();
+  s->caches.resize(max_slots);
+  s->busy.assign(max_slots, 0);
+  for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s, i);
+  *out = s;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_server_submit(hotrg_server s, const hotrg_request* r, uint64_t* ticket) {
+  if (!s || !r || !ticket) return HOTRG_EINVAL;
+  if (r->d_cut < 1 || r->n_steps < 1 || r->n_steps > 200 || r->precision < HOTRG_FP64 ||
+      r->precision > HOTRG_BF16X6 || !(r->beta * r->J >= 0))
+    return HOTRG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (s->stop) return HOTRG_ESTATE;
+  Job j{s->next_ticket++, *r, s->now()};
+  s->queue.push_back(j);
+  s->submitted += 1;
+  *ticket = j.ticket;
+  s->cv.notify_all();
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_server_poll(hotrg_server s, uint64_t ticket, hotrg_result* out) {
+  if (!s || !out) return HOTRG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->results.find(ticket);
+  if (it == s->results.end()) return ticket < s->next_ticket ? HOTRG_EPENDING : HOTRG_EINVAL;
+  *out = it->second;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_server_wait(hotrg_server s, uint64_t ticket, hotrg_result* out) {
+  if (!s || !out) return HOTRG_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  if (ticket == 0 || ticket >= s->next_ticket) return HOTRG_EINVAL;
+  s->cv.wait(lk, [&] { return s->results.count(ticket) > 0; });
+  *out = s->results[ticket];
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_server_drain(hotrg_server s) {
+  if (!s) return HOTRG_EINVAL;
+  std::unique_lock<std::mutex> lk(s->mu);
+  s->cv.wait(lk, [&] { return s->queue.empty() && s->running == 0; });
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_server_get_stats(hotrg_server s, hotrg_server_stats* o) {
+  if (!s || !o) return HOTRG_EINVAL;
+  std::lock_guard<std::mutex> lk(s->mu);
+  memset(o, 0, sizeof(*o));
+  o->submitted = s->submitted;
+  o->completed = s->completed;
+  o->failed = s->failed;
+  o->bytes_in_use = s->bytes_in_use;
+  o->peak_bytes = s->peak_bytes;
+  o->plans_created = s->created;
+  o->plans_evicted = s->evicted;
+  o->queue_depth = (int)s->queue.size();
+  o->busy_slots = s->running;
+  return HOTRG_OK;
+}
+
+void hotrg_server_destroy(hotrg_server s) {
+  if (!s) return;
+  {
+    std::lock_guard<std::mutex> lk(s->mu);
+    s->stop = true;
+    s->cv.notify_all();
+  }
+  for (auto& t : s->workers) t.join();
+  delete s;
+}
+
+}  // extern "C"
