@@ -81,12 +81,16 @@ typedef struct {
   int fixed_w_grad;     /* 1: backward holds every w fixed (SM Sec. E view of w as
                            independent parameters); 0: full derivative through the eigh  */
   double eigh_broadening; /* eta_rel in F = d / (d^2 + eta_rel * lam_1^2); <= 0 -> 1e-12 */
+  int gram_split_from_step; /* 1-based; the Gram matrix of split steps before it is formed
+                               in FP64 (the eigensolve is the step most sensitive to
+                               rounding); <= split_from_step: same as the contractions   */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
 
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
- * fixed_w_grad = 0, eigh_broadening = 1e-12.  d0, d_cut, n_steps as given. */
+ * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0.
+ * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
 /* Device bytes a plan with this config would allocate (for admission control). */

@@ -434,18 +434,32 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   double* lk = p->lam[k - 1];
   const int N = (int)s.N;
   hotrg_status r;
-  if (s.split) r = gram_split(p, s, T, p->Escr);
+  if (s.split && k >= p->cfg.gram_split_from_step) r = gram_split(p, s, T, p->Escr);
   else r = gram_f64(p, s, T, p->Abuf, p->Bbuf, p->Escr);
   if (r != HOTRG_OK) return r;
   {
   Stage sc(p, kStEigh);
-  cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                         CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc, p->work,
-                                         p->lwork, p->info);
-  if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
+  CK(diag_trace(p->Escr, N, p->scal + 3, st));
+  int ncols = N;
+  if (p->cfg.want_grad || s.Xp >= N) {
+    // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
+    cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                           CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc,
+                                           p->work, p->lwork, p->info);
+    if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
+  } else {
+    // forward only: the D'+1 largest eigenpairs (D' kept, one more for the gap)
+    int meig = 0;
+    cusolverStatus_t cs = cusolverDnDsyevdx(p->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                            CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, N,
+                                            p->Escr, N, 0.0, 0.0, N - s.Xp, N, &meig, p->wasc,
+                                            p->work, p->lwork, p->info);
+    if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevdx failed");
+    ncols = s.Xp + 1;
+  }
   CK(eigh_info_check(p->info, p->err, st));
-  CK(eig_desc(p->Escr, p->wasc, N, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
-  CK(eig_diag(lk, N, s.Xp, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
+  CK(eig_desc(p->Escr, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
+  CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
   }
   if (s.split) r = contract_split(p, s, T, Ek, Tout);
   else r = contract_f64(p, s, T, Ek, Tout);
@@ -678,6 +692,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->want_grad = 1;
   c->fixed_w_grad = 0;
   c->eigh_broadening = 1e-12;
+  c->gram_split_from_step = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -809,6 +824,16 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
         CUSOLVER_STATUS_SUCCESS)
       return cleanup(HOTRG_ECUDA);
     if (l > lw) lw = l;
+    if (!cfg->want_grad && g.Xp < g.N) {
+      int meig = 0;
+      l = 0;
+      if (cusolverDnDsyevdx_bufferSize(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                       CUBLAS_FILL_MODE_LOWER, (int)g.N, p->Escr, (int)g.N, 0.0,
+                                       0.0, (int)g.N - g.Xp, (int)g.N, &meig, p->wasc, &l) !=
+          CUSOLVER_STATUS_SUCCESS)
+        return cleanup(HOTRG_ECUDA);
+      if (l > lw) lw = l;
+    }
   }
   p->lwork = lw;
   ALC(p->work, (long long)lw);

@@ -225,17 +225,18 @@ __global__ void trace_lnz_kernel(const double* __restrict__ T, int P, int Q,
   }
 }
 
-// Eigen post-processing.  cuSOLVER returns eigenvalues ascending and the
-// eigenvectors as the columns of a column-major matrix, i.e. eigenvector a is
-// the contiguous row a of `asc`.  Write them descending: row alpha of `desc`
-// is eigenvector N-1-alpha, flipped so that its largest-magnitude component
-// (lowest index on ties) is positive.  One block per eigenvector.
+// Eigen post-processing.  cuSOLVER returns `ncols` eigenvalues ascending (the
+// largest ones) and their eigenvectors as the columns of a column-major
+// matrix, i.e. eigenvector a is the contiguous row a of `asc`.  Write them
+// descending: row alpha of `desc` is eigenvector ncols-1-alpha, flipped so
+// that its largest-magnitude component (lowest index on ties) is positive.
+// One block per eigenvector.
 __global__ void eig_desc_kernel(const double* __restrict__ asc, const double* __restrict__ w_asc,
-                                int N, int rows_out, double* __restrict__ desc,
+                                int N, int ncols, int rows_out, double* __restrict__ desc,
                                 double* __restrict__ lam_desc) {
   const int alpha = blockIdx.x;
   if (alpha >= rows_out) return;
-  const double* src = asc + (long long)(N - 1 - alpha) * N;
+  const double* src = asc + (long long)(ncols - 1 - alpha) * N;
   double best = -1.0;
   int bi = 0;
   for (int i = threadIdx.x; i < N; i += blockDim.x) {
@@ -262,18 +263,31 @@ __global__ void eig_desc_kernel(const double* __restrict__ asc, const double* __
   double* dst = desc + (long long)alpha * N;
   for (int i = threadIdx.x; i < N; i += blockDim.x) dst[i] = sgn * src[i];
   if (alpha == 0)
-    for (int i = threadIdx.x; i < N; i += blockDim.x) lam_desc[i] = w_asc[N - 1 - i];
+    for (int i = threadIdx.x; i < ncols; i += blockDim.x) lam_desc[i] = w_asc[ncols - 1 - i];
 }
 
-// trunc_err = sum(lam[Dp:]) / sum(lam); gap = (lam[Dp-1] - lam[Dp]) / lam[0].
-__global__ void eig_diag_kernel(const double* __restrict__ lam, int N, int Dp, double* trunc,
-                                double* gap) {
+// Trace of an N x N matrix (before the eigensolver overwrites it).
+__global__ void diag_trace_kernel(const double* __restrict__ G, int N, double* out) {
+  __shared__ double s[256];
+  double a = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) a += G[(long long)i * N + i];
+  s[threadIdx.x] = a;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = s[0];
+}
+
+// trunc_err = sum of discarded eigenvalues / sum of all (= trace(G));
+// gap = (lam[Dp-1] - lam[Dp]) / lam[0].  `nlam` eigenvalues (descending) are
+// known; the discarded sum is trace - sum of the kept ones.
+__global__ void eig_diag_kernel(const double* __restrict__ lam, int nlam, int N, int Dp,
+                                const double* __restrict__ trace, double* trunc, double* gap) {
   __shared__ double s_all[256], s_cut[256];
   double a = 0.0, c = 0.0;
-  for (int i = threadIdx.x; i < N; i += blockDim.x) {
-    a += lam[i];
-    if (i >= Dp) c += lam[i];
-  }
+  for (int i = threadIdx.x; i < Dp; i += blockDim.x) a += lam[i];
   s_all[threadIdx.x] = a;
   s_cut[threadIdx.x] = c;
   __syncthreads();
@@ -285,8 +299,9 @@ __global__ void eig_diag_kernel(const double* __restrict__ lam, int N, int Dp, d
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    *trunc = s_all[0] != 0.0 ? s_cut[0] / s_all[0] : 0.0;
-    *gap = (Dp < N && lam[0] != 0.0) ? (lam[Dp - 1] - lam[Dp]) / lam[0] : 0.0;
+    const double tot = *trace;
+    *trunc = tot != 0.0 ? (tot - s_all[0]) / tot : 0.0;
+    *gap = (Dp < N && Dp < nlam && lam[0] != 0.0) ? (lam[Dp - 1] - lam[Dp]) / lam[0] : 0.0;
   }
 }
 
@@ -428,17 +443,23 @@ cudaError_t trace_lnz(const double* T, int P, int Q, const double* log_norms, in
   return cudaGetLastError();
 }
 
-cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int rows_out, double* desc,
-                     double* lam_desc, cudaStream_t st) {
+cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int ncols, int rows_out,
+                     double* desc, double* lam_desc, cudaStream_t st) {
   count_launch();
-  eig_desc_kernel<<<rows_out, 256, 0, st>>>(asc, w_asc, N, rows_out, desc, lam_desc);
+  eig_desc_kernel<<<rows_out, 256, 0, st>>>(asc, w_asc, N, ncols, rows_out, desc, lam_desc);
   return cudaGetLastError();
 }
 
-cudaError_t eig_diag(const double* lam, int N, int Dp, double* trunc, double* gap,
-                     cudaStream_t st) {
+cudaError_t diag_trace(const double* G, int N, double* out, cudaStream_t st) {
   count_launch();
-  eig_diag_kernel<<<1, 256, 0, st>>>(lam, N, Dp, trunc, gap);
+  diag_trace_kernel<<<1, 256, 0, st>>>(G, N, out);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_diag(const double* lam, int nlam, int N, int Dp, const double* trace, double* trunc,
+                     double* gap, cudaStream_t st) {
+  count_launch();
+  eig_diag_kernel<<<1, 256, 0, st>>>(lam, nlam, N, Dp, trace, trunc, gap);
   return cudaGetLastError();
 }
 

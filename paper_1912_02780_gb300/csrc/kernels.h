@@ -25,9 +25,11 @@ cudaError_t frob_normalize(double* x, long long n, double* partial, int max_part
                            int sms);
 cudaError_t trace_lnz(const double* T, int P, int Q, const double* log_norms, int n, double* out,
                       double* trace_out, int* err, cudaStream_t st);
-cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int rows_out, double* desc,
-                     double* lam_desc, cudaStream_t st);
-cudaError_t eig_diag(const double* lam, int N, int Dp, double* trunc, double* gap, cudaStream_t st);
+cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int ncols, int rows_out,
+                     double* desc, double* lam_desc, cudaStream_t st);
+cudaError_t diag_trace(const double* G, int N, double* out, cudaStream_t st);
+cudaError_t eig_diag(const double* lam, int nlam, int N, int Dp, const double* trace, double* trunc,
+                     double* gap, cudaStream_t st);
 cudaError_t eigh_info_check(const int* info, int* err, cudaStream_t st);
 cudaError_t seed_trace_adjoint(double* E, int P, int Q, const double* tr, cudaStream_t st, int sms);
 cudaError_t eigh_adj_scale(double* S, int nd, int Dp, const double* lam, double eta_rel,
