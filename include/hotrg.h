@@ -84,12 +84,16 @@ typedef struct {
   int gram_split_from_step; /* 1-based; the Gram matrix of split steps before it is formed
                                in FP64 (the eigensolve is the step most sensitive to
                                rounding); <= split_from_step: same as the contractions   */
+  int hi_precision_steps;   /* with HOTRG_BF16X6: the first hi_precision_steps split steps use
+                               four bf16 planes (10 products, ~32 significant bits) instead of
+                               three; these steps weigh most in ln Z / N (weight 2^-k)     */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
 
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
- * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0.
+ * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
+ * hi_precision_steps = 2.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
@@ -219,7 +223,7 @@ unsigned long long hotrg_kernel_launches(void);
  * 0 = a single chunk; K must be a multiple of 8) or by the FP64 GEMM.  They
  * allocate and free temporary device memory and synchronise the device. */
 hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
-                                    const double* B, double* C);
+                                    const double* B, double* C);   /* planes: 2, 3 or 4 */
 hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const double* B, double* C);
 
 /* Allocation-free variant of hotrg_gemm_split_check (the paper has no

@@ -46,7 +46,8 @@ class hotrg_config(ctypes.Structure):
     _fields_ = [("d0", ctypes.c_int), ("d_cut", ctypes.c_int), ("n_steps", ctypes.c_int),
                 ("precision", ctypes.c_int), ("split_from_step", ctypes.c_int),
                 ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
-                ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int)]
+                ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
+                ("hi_precision_steps", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -139,7 +140,8 @@ def _p(a: np.ndarray):
 
 def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_step: int = 1,
                 want_grad: bool = True, fixed_w_grad: bool = False,
-                eigh_broadening: float = 1e-12, gram_split_from_step: int = 0) -> hotrg_config:
+                eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
+                hi_precision_steps: int = 2) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -148,6 +150,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.fixed_w_grad = int(bool(fixed_w_grad))
     c.eigh_broadening = eigh_broadening
     c.gram_split_from_step = gram_split_from_step
+    c.hi_precision_steps = hi_precision_steps
     return c
 
 
@@ -171,9 +174,10 @@ class Plan:
     def __init__(self, d0: int, d_cut: int, n_steps: int, precision="fp64",
                  split_from_step: int = 1, want_grad: bool = True, fixed_w_grad: bool = False,
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
-                 gram_split_from_step: int = 0):
+                 gram_split_from_step: int = 0, hi_precision_steps: int = 2):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
-                               fixed_w_grad, eigh_broadening, gram_split_from_step)
+                               fixed_w_grad, eigh_broadening, gram_split_from_step,
+                               hi_precision_steps)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

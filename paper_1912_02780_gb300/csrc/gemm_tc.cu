@@ -559,6 +559,13 @@ cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cuda
 void tc_set_pairs(TcGemm& g, int nplanes) {
   // Product 0 must be hi * hi: it is accumulated exactly in its own TMEM buffer.
   g.nplanes = nplanes;
+  if (nplanes == 4) {
+    // all products with plane-sum <= 3: hi*hi first, then smallest first
+    const int a[10] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0}, b[10] = {0, 0, 1, 2, 3, 0, 1, 2, 0, 1};
+    g.npairs = 10;
+    for (int i = 0; i < 10; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
+    return;
+  }
   if (nplanes == 2) {
     const int a[3] = {0, 1, 0}, b[3] = {0, 0, 1};
     g.npairs = 3;
@@ -588,6 +595,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
     if (g.N > 64) return launch<128, 3>(A, B, g, stream, num_sms);
     return launch<64, 3>(A, B, g, stream, num_sms);
   }
+  if (g.nplanes == 4) return launch<64, 4>(A, B, g, stream, num_sms);
   return cudaErrorInvalidValue;
 }
 

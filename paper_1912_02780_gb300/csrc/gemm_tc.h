@@ -18,7 +18,7 @@ struct TcGemm {
   int M, N, K;
   int nplanes;               // operand planes (2 or 3)
   int npairs;                // products formed per K slab
-  int pa[6], pb[6];          // plane of A / of B for each product
+  int pa[10], pb[10];        // plane of A / of B for each product (product 0 = hi * hi)
   int kchunk;                // K-blocks (of 64) per FP32 accumulation chunk; chunks are summed
                              // in compensated float-float; >= ceil(K/64) means one chunk
   IMap cm, cn;               // output element (m, n) at C + cm(m) + cn(n)
@@ -33,8 +33,8 @@ struct TcGemm {
   int* err;                  // device error word
 };
 
-// Set the products of a precision: nplanes = 2 -> {hh, hl, lh};
-// nplanes = 3 -> {hh, hm, mh, hl, mm, lh}.
+// Set the products of a precision: all plane pairs (i, j) with
+// i + j <= nplanes - 1 (3, 6 or 10 products for 2, 3 or 4 planes), hi * hi first.
 void tc_set_pairs(TcGemm& g, int nplanes);
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,

@@ -46,6 +46,7 @@ struct StepGeom {
   int X, Y, Xp;
   long long N;        // X * X
   bool split;
+  int np;             // bf16 planes of the split GEMM operands (0: FP64 step)
   int yc64, ycs;      // y-chunk of the FP64 and split stage buffers
 };
 
@@ -57,8 +58,9 @@ struct Layout {
   long long chunk64 = 0, chunkS = 0;       // elements
   long long splitT = 0, splitG = 0, splitW1 = 0, splitW3 = 0;   // elements per plane
   long long totalE = 0, totalT = 0, totalLam = 0;
-  int np = 0;
-  bool any_split = false;
+  int np = 0;          // planes of the configured split precision
+  int np_max = 0;      // most planes of any step (4 on the high-precision steps)
+  bool any_split = false, any_hi = false;
 };
 
 int planes_of(int precision) {
@@ -77,6 +79,12 @@ bool build_layout(const hotrg_config& c, Layout& L) {
     long long Xp = s.N < c.d_cut ? s.N : c.d_cut;
     s.Xp = (int)Xp;
     s.split = L.np > 0 && k >= c.split_from_step && X % 8 == 0 && Y % 8 == 0 && Xp % 8 == 0;
+    s.np = 0;
+    if (s.split) {
+      s.np = (L.np == 3 && k < c.split_from_step + c.hi_precision_steps) ? 4 : L.np;
+      if (s.np > L.np_max) L.np_max = s.np;
+      if (s.np == 4) L.any_hi = true;
+    }
     long long per_y = X * X * Xp * Y;
     long long a = kChunkF64 / per_y;
     s.yc64 = (int)(a < 1 ? 1 : (a > Y ? Y : a));
@@ -145,6 +153,7 @@ struct hotrg_plan_s {
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
+  double* F64 = nullptr;  // same, FP64, for the four-plane steps
   double* splitk = nullptr;   // FP64 split-K partials (deterministic reduction)
   bool have_fwd = false, fwd_ising = false;
   std::string last_error;
@@ -228,7 +237,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (!c) return HOTRG_EINVAL;
   if (c->d0 < 1 || c->d_cut < 1 || c->n_steps < 1 || c->n_steps > 200) return HOTRG_EINVAL;
   if (c->precision < HOTRG_FP64 || c->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
-  if (c->split_from_step < 1) return HOTRG_EINVAL;
+  if (c->split_from_step < 1 || c->hi_precision_steps < 0) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -251,16 +260,16 @@ GemmF64 g64(const hotrg_plan p, const double* A, IMap am, IMap ak, const double*
   return g;
 }
 
-TcGemm tcg(const hotrg_plan p, int M, int N, int K, IMap cm, IMap cn, int mode, void* C,
+TcGemm tcg(const hotrg_plan p, int np, int M, int N, int K, IMap cm, IMap cn, int mode, void* C,
            long long out_plane_stride) {
   TcGemm g;
   memset(&g, 0, sizeof(g));
-  tc_set_pairs(g, p->L.np);
+  tc_set_pairs(g, np);
   g.M = M; g.N = N; g.K = K;
   g.kchunk = kGridSeg / 64;   // accumulation chunk = grid segment of the operand split
   g.cm = cm; g.cn = cn;
   g.out_mode = mode;
-  g.out_planes = p->L.np;
+  g.out_planes = np;
   g.out_plane_stride = out_plane_stride;
   g.C = C;
   g.alpha = 1.f;
@@ -278,9 +287,20 @@ cudaError_t gsplit(const hotrg_plan p, const double* src, IMap rm, IMap km, int 
   return grid_split(src, lim_of(p, src, sizeof(double)), rm, km, rows, K, np, stride, dst, p->err,
                     p->stream, p->sms);
 }
-cudaError_t fsplit(const hotrg_plan p, int rows, int K, long long stride, __nv_bfloat16* dst) {
-  return grid_split(p->F32, lim_of(p, p->F32, sizeof(float)), map_lin(K), map_lin(1), rows, K,
-                    p->L.np, stride, dst, p->err, p->stream, p->sms);
+// Split a GEMM output kept in the staging buffer: FP32 for three planes, FP64
+// for four (a float cannot feed more than three bf16 planes).
+cudaError_t fsplit(const hotrg_plan p, int np, int rows, int K, long long stride,
+                   __nv_bfloat16* dst) {
+  if (np == 4)
+    return grid_split(p->F64, lim_of(p, p->F64, sizeof(double)), map_lin(K), map_lin(1), rows, K,
+                      np, stride, dst, p->err, p->stream, p->sms);
+  return grid_split(p->F32, lim_of(p, p->F32, sizeof(float)), map_lin(K), map_lin(1), rows, K, np,
+                    stride, dst, p->err, p->stream, p->sms);
+}
+// Output mode and buffer of a GEMM whose result is split again.
+int stage_mode(int np) { return np == 4 ? kOutF64 : kOutF32; }
+void* stage_buf(const hotrg_plan p, int np) {
+  return np == 4 ? static_cast<void*>(p->F64) : static_cast<void*>(p->F32);
 }
 
 TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long stride) {
@@ -315,7 +335,7 @@ hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* 
 }
 
 hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double* G) {
-  const int X = s.X, Y = s.Y, np = p->L.np;
+  const int X = s.X, Y = s.Y, np = s.np;
   const long long XY2 = (long long)X * Y * Y, Y2 = (long long)Y * Y;
   cudaStream_t st = p->stream;
   const long long sT = p->L.splitT, sG = p->L.splitG;
@@ -326,14 +346,16 @@ hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double
   }
   Stage sc(p, kStGram);
   TcOperand ta = opnd(p->pTA, X * Y, X * Y, np, sT), tb = opnd(p->pTB, X * Y, X * Y, np, sT);
-  CK(tc_gemm(ta, ta, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutF32, p->F32, 0),
+  CK(tc_gemm(ta, ta, tcg(p, np, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2),
+                         stage_mode(np), stage_buf(p, np), 0),
              st, p->sms));
-  CK(fsplit(p, X * X, Y * Y, sG, p->pA));
-  CK(tc_gemm(tb, tb, tcg(p, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2), kOutF32, p->F32, 0),
+  CK(fsplit(p, np, X * X, Y * Y, sG, p->pA));
+  CK(tc_gemm(tb, tb, tcg(p, np, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2),
+                         stage_mode(np), stage_buf(p, np), 0),
              st, p->sms));
-  CK(fsplit(p, X * X, Y * Y, sG, p->pB));
+  CK(fsplit(p, np, X * X, Y * Y, sG, p->pB));
   TcOperand a = opnd(p->pA, X * X, Y * Y, np, sG), b = opnd(p->pB, X * X, Y * Y, np, sG);
-  CK(tc_gemm(a, b, tcg(p, X * X, X * X, Y * Y, map2(X, X, (long long)X * X * X),
+  CK(tc_gemm(a, b, tcg(p, np, X * X, X * X, Y * Y, map2(X, X, (long long)X * X * X),
                        map2(X, 1, (long long)X * X), kOutF64, G, 0),
              st, p->sms));
   return HOTRG_OK;
@@ -374,7 +396,7 @@ hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, cons
 
 hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, const double* Ek,
                             double* Tout) {
-  const int X = s.X, Y = s.Y, Xp = s.Xp, np = p->L.np;
+  const int X = s.X, Y = s.Y, Xp = s.Xp, np = s.np;
   const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
   const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X;
   cudaStream_t st = p->stream;
@@ -396,27 +418,27 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     {
     Stage sc(p, kStS1);
     CK(tc_gemm(w1, t1,
-               tcg(p, Xp * X, yc * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
-                   kOutF32, p->F32, 0),
+               tcg(p, np, Xp * X, yc * X * Y, X, map2(X, Y, XY),
+                   map3(Y, X, 1, Xp * XY, X * Xp * XY), stage_mode(np), stage_buf(p, np), 0),
                st, p->sms));
-    CK(fsplit(p, yc * X * Xp, X * Y, sC, p->pU));
+    CK(fsplit(p, np, yc * X * Xp, X * Y, sC, p->pU));
     }
     const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
     {
     Stage sc(p, kStS2);
     CK(tc_gemm(u, pp,
-               tcg(p, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
-                   map2(X, 1, X2), kOutF32, p->F32, 0),
+               tcg(p, np, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
+                   map2(X, 1, X2), stage_mode(np), stage_buf(p, np), 0),
                st, p->sms));
     }
     {
     Stage sc(p, kStPrep);
-    CK(fsplit(p, yc * Xp * Y, X * X, sC, p->pV));
+    CK(fsplit(p, np, yc * Xp * Y, X * X, sC, p->pV));
     }
     const TcOperand v = opnd(p->pV, yc * Xp * Y, X * X, np, sC);
     Stage sc(p, kStS3);
     CK(tc_gemm(v, w3,
-               tcg(p, yc * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1), kOutF64,
+               tcg(p, np, yc * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1), kOutF64,
                    Tout + (long long)y0 * Y * Xp2, 0),
                st, p->sms));
   }
@@ -489,18 +511,18 @@ hotrg_status run_forward(hotrg_plan p) {
 // both operands from their FP64 sources through the same index maps, FP64
 // output, optional accumulation) when the step runs split and the operands fit
 // the plane buffers, else on the FP64 GEMM.
-cudaError_t run_gemm(hotrg_plan p, bool split, const GemmF64& g) {
+cudaError_t run_gemm(hotrg_plan p, int np, const GemmF64& g) {
+  const bool split = np > 0;
   const long long cap = p->L.chunkS;
   const bool ok = split && p->L.any_split && g.K % 8 == 0 && (g.beta == 0.0 || g.beta == 1.0) &&
                   (long long)g.M * g.K <= cap && (long long)g.N * g.K <= cap && g.K > 0;
   if (!ok) return gemm_f64(g, p->stream, p->sms);
-  const int np = p->L.np;
   cudaError_t e = grid_split(g.A, g.a_lim, g.am, g.ak, g.M, g.K, np, cap, p->pU, p->err,
                              p->stream, p->sms);
   if (e != cudaSuccess) return e;
   e = grid_split(g.B, g.b_lim, g.bn, g.bk, g.N, g.K, np, cap, p->pV, p->err, p->stream, p->sms);
   if (e != cudaSuccess) return e;
-  TcGemm t = tcg(p, g.M, g.N, g.K, g.cm, g.cn, kOutF64, g.C, 0);
+  TcGemm t = tcg(p, np, g.M, g.N, g.K, g.cm, g.cn, kOutF64, g.C, 0);
   t.alpha = (float)g.alpha;
   t.accumulate = g.beta != 0.0 ? 1 : 0;
   return tc_gemm(opnd(p->pU, g.M, g.K, np, cap), opnd(p->pV, g.N, g.K, np, cap), t, p->stream,
@@ -510,6 +532,7 @@ cudaError_t run_gemm(hotrg_plan p, bool split, const GemmF64& g) {
 hotrg_status step_backward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
   const bool sp = s.split;
+  const int snp = s.np;
   const int X = s.X, Y = s.Y, Xp = s.Xp;
   const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
   const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X, YXp2 = (long long)Y * Xp2;
@@ -528,33 +551,33 @@ hotrg_status step_backward(hotrg_plan p, int k) {
     const double* Ty = T + (long long)y0 * Y;
     const double* Eby = Eb + (long long)y0 * YXp2;
     // recompute U and V of this chunk (as in the forward)
-    CK(run_gemm(p, sp, g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
+    CK(run_gemm(p, snp, g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
                     map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY), Xp * X, yc * X * Y, X,
                     1.0, 0.0)));
-    CK(run_gemm(p, sp, g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
+    CK(run_gemm(p, snp, g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
                     map3(Xp, X, Y * X2, X, Xp * Y * X2), map2(X, 1, X2), yc * X * Xp, Y * X,
                     X * Y, 1.0, 0.0)));
     // P[(y a i)][(k z)] = sum_b Tbar'[a b y z] w[i k b]
-    CK(run_gemm(p, sp, g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
+    CK(run_gemm(p, snp, g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
                     p->Pb, map3(Y, Xp, 1, X2 * Y, (long long)Xp * X2 * Y), map2(X, Y, XY),
                     yc * Xp * Y, X * X, Xp, 1.0, 0.0)));
     // Q[(y a i)][(b j)] = sum_{k z} P T[b k j z]
-    CK(run_gemm(p, sp, g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
+    CK(run_gemm(p, snp, g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
                     map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0)));
     // upper copy: Tbar[a i y j] += sum_{A b} w[a b A] Q[y A i b j]
-    CK(run_gemm(p, sp, g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
+    CK(run_gemm(p, snp, g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
                     map2(X, Y, X * XY), p->Tbar + (long long)y0 * Y, map_lin(XY2),
                     map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0)));
     // lower copy: Tbar[b k j z] += sum_{y i A} U[y i A b j] P[y A z i k]
-    CK(run_gemm(p, sp, g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
+    CK(run_gemm(p, snp, g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
                     map2(Y, 1, Y), map3(Xp, X, X * XY, XY, (long long)Xp * X * XY), p->Tbar,
                     map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0)));
     // w carrying alpha: wbT[A][(a b)] += sum_{y i j} T[a i y j] Q[y A i b j]
-    CK(run_gemm(p, sp, g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
+    CK(run_gemm(p, snp, g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
                     map3(Y, X, 1, XY, (long long)Xp * X * XY), p->wbT, map_lin(X), map2(X, 1, N),
                     X, Xp * X, yc * X * Y, 1.0, 1.0)));
     // w carrying beta: wbT[B][(i k)] += sum_{y A z} V[y A z][(i k)] Tbar'[A B y z]
-    CK(run_gemm(p, sp, g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
+    CK(run_gemm(p, snp, g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
                     map_lin(1), map3(Y, Xp, Xp2, Xp, YXp2), p->wbT, map_lin(1), map_lin(N),
                     X * X, Xp, yc * Xp * Y, 1.0, 1.0)));
   }
@@ -580,25 +603,25 @@ hotrg_status step_backward(hotrg_plan p, int k) {
     {
       // Gram halves again (A, B of the forward), FP64 output
       const long long XY2g = (long long)X * Y * Y, Y2g = (long long)Y * Y;
-      CK(run_gemm(p, sp, g64(p, T, map2(Y, 1, XY2g), map2(Y, Y, Y2g), T, map2(Y, 1, XY2g),
+      CK(run_gemm(p, snp, g64(p, T, map2(Y, 1, XY2g), map2(Y, Y, Y2g), T, map2(Y, 1, XY2g),
                              map2(Y, Y, Y2g), p->Abuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
                              X * Y, X * Y, 1.0, 0.0)));
-      CK(run_gemm(p, sp, g64(p, T, map2(Y, Y, XY2g), map2(Y, 1, Y2g), T, map2(Y, Y, XY2g),
+      CK(run_gemm(p, snp, g64(p, T, map2(Y, Y, XY2g), map2(Y, 1, Y2g), T, map2(Y, Y, XY2g),
                              map2(Y, 1, Y2g), p->Bbuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
                              X * Y, X * Y, 1.0, 0.0)));
     }
     const long long X3 = X2 * X;
     // Abar[(x1 x1'')][(j j')] = sum_{x2 x2''} Gbar[x1 x2 x1'' x2''] B[(x2 x2'')][(j j')]
-    CK(run_gemm(p, sp, g64(p, p->Gb, map2(X, X, X3), map2(X, 1, X2), p->Bbuf, map_lin(1), map_lin(Y2),
+    CK(run_gemm(p, snp, g64(p, p->Gb, map2(X, X, X3), map2(X, 1, X2), p->Bbuf, map_lin(1), map_lin(Y2),
                     p->Abar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
-    CK(run_gemm(p, sp, g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
+    CK(run_gemm(p, snp, g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
                     p->Bbar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
     // Tbar[a i y j] += 2 sum_{c k} Abar[a j c k] T[c i y k]
-    CK(run_gemm(p, sp, g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
+    CK(run_gemm(p, snp, g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
                     map2(Y, 1, XY2), p->Tbar, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, X * Y,
                     2.0, 1.0)));
     // Tbar[b k j z] += 2 sum_{d m} Bbar[b j d m] T[d k m z]
-    CK(run_gemm(p, sp, g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
+    CK(run_gemm(p, snp, g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
                     map2(Y, Y, XY2), p->Tbar, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y,
                     2.0, 1.0)));
   }
@@ -693,6 +716,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->fixed_w_grad = 0;
   c->eigh_broadening = 1e-12;
   c->gram_split_from_step = 0;
+  c->hi_precision_steps = 2;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -714,10 +738,11 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
     b.add(L.maxT, 8 * 3);
   }
   if (L.any_split) {
-    b.add(L.splitT * L.np, 2 * 4);
-    b.add(L.splitG * L.np, 2 * 2);
-    b.add((L.splitW1 + L.splitW3) * L.np, 2);
-    b.add(L.chunkS * L.np, 2 * 2);
+    b.add(L.splitT * L.np_max, 2 * 4);
+    b.add(L.splitG * L.np_max, 2 * 2);
+    b.add((L.splitW1 + L.splitW3) * L.np_max, 2);
+    b.add(L.chunkS * L.np_max, 2 * 2);
+    if (L.any_hi) b.add(L.chunkS > L.splitG ? L.chunkS : L.splitG, 8);
     b.add(L.chunkS > L.splitG ? L.chunkS : L.splitG, 4);
   }
   b.add(kSplitK, 8);
@@ -800,7 +825,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   ALC(p->err, 4);
   ALC(p->info, 4);
   if (L.any_split) {
-    const int np = L.np;
+    const int np = L.np_max;
     ALC(p->pTA, L.splitT * np);
     ALC(p->pTB, L.splitT * np);
     ALC(p->pT1, L.splitT * np);
@@ -812,6 +837,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     ALC(p->pU, L.chunkS * np);
     ALC(p->pV, L.chunkS * np);
     ALC(p->F32, L.chunkS > L.splitG ? L.chunkS : L.splitG);
+    if (L.any_hi) ALC(p->F64, L.chunkS > L.splitG ? L.chunkS : L.splitG);
   }
   if (cusolverDnCreate(&p->solver) != CUSOLVER_STATUS_SUCCESS) return cleanup(HOTRG_ECUDA);
   if (cusolverDnSetStream(p->solver, p->stream) != CUSOLVER_STATUS_SUCCESS)
@@ -998,7 +1024,7 @@ hotrg_status hotrg_device_supports_split(void) {
 
 hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
                                     const double* B, double* C) {
-  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || (planes != 2 && planes != 3) || !A || !B || !C)
+  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || planes < 2 || planes > 4 || !A || !B || !C)
     return HOTRG_EINVAL;
   hotrg_status status = HOTRG_OK;
   double *dA = nullptr, *dB = nullptr, *dC = nullptr;

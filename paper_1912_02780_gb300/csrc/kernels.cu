@@ -99,20 +99,28 @@ __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_li
         else b0 = __double2bfloat16(vd[i]);
         dst[o] = b0;
         if (nplanes > 1) {
-          __nv_bfloat16 b1, b2;
+          __nv_bfloat16 b1, b2, b3;
           if constexpr (sizeof(SrcT) == 4) {
             // float source: the remainders are exact in float
             const float rem = v[i] - __bfloat162float(b0);
             b1 = __float2bfloat16_rn(rem);
-            b2 = __float2bfloat16_rn(rem - __bfloat162float(b1));
+            const float rem2 = rem - __bfloat162float(b1);
+            b2 = __float2bfloat16_rn(rem2);
+            b3 = __float2bfloat16_rn(rem2 - __bfloat162float(b2));
           } else {
-            // double source: keep the bits a float would drop
-            const double rem = vd[i] - (double)__bfloat162float(b0);
-            b1 = __double2bfloat16(rem);
-            b2 = __double2bfloat16(rem - (double)__bfloat162float(b1));
+            // double source: the first remainder as a float pair keeps the bits
+            // a float would drop (enough for four planes), the rest in float
+            const double remd = vd[i] - (double)__bfloat162float(b0);
+            const float rh = (float)remd;
+            const float rl = (float)(remd - (double)rh);
+            b1 = __float2bfloat16_rn(rh);
+            const float rem2 = (rh - __bfloat162float(b1)) + rl;
+            b2 = __float2bfloat16_rn(rem2);
+            b3 = __float2bfloat16_rn(rem2 - __bfloat162float(b2));
           }
           dst[plane_stride + o] = b1;
           if (nplanes > 2) dst[2 * plane_stride + o] = b2;
+          if (nplanes > 3) dst[3 * plane_stride + o] = b3;
         }
       }
     }
@@ -390,6 +398,7 @@ cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, i
   // Plane 0 on the grid only for three planes; with two planes a floating
   // plane 0 keeps more bits for small elements (see the comment above).
   const int gridded = nplanes >= 3 ? 1 : 0;
+  if (nplanes < 1 || nplanes > 4) return cudaErrorInvalidValue;
   const int seg = K < kGridSeg ? K : kGridSeg;
   const long long work = (long long)rows * ((K + seg - 1) / seg);
   if (work == 0) return cudaSuccess;

@@ -30,7 +30,7 @@ def test_gemm_f64_kernel(M, N, K):
     assert np.max(np.abs(C - A @ B.T)) < 1e-12 * np.max(np.abs(A) @ np.abs(B).T)
 
 
-@pytest.mark.parametrize("planes,kchunk", [(2, 0), (3, 0), (3, 2), (2, 2), (3, 3)])
+@pytest.mark.parametrize("planes,kchunk", [(2, 0), (3, 0), (3, 2), (2, 2), (3, 3), (4, 2)])
 @pytest.mark.parametrize("M,N,K", [(128, 128, 64), (300, 200, 520), (1000, 72, 4096), (5, 700, 8)])
 def test_gemm_split_kernel(planes, kchunk, M, N, K):
     rng = np.random.default_rng(M * 7 + N + K)
@@ -39,8 +39,9 @@ def test_gemm_split_kernel(planes, kchunk, M, N, K):
     scale = np.abs(A) @ np.abs(B).T
     err = np.max(np.abs(C - A @ B.T) / scale)
     # three planes with accumulation chunks of 128 (the grid segment): exact hi*hi sums
-    exact = planes == 3 and kchunk == 2
-    bound = {2: 3e-5, 3: (5e-8 if K >= 512 else 1e-6) if exact else 4e-6}[planes]
+    exact = planes >= 3 and kchunk == 2
+    bound = {2: 3e-5, 3: (5e-8 if K >= 512 else 1e-6) if exact else 4e-6,
+             4: 5e-9 if K >= 512 else 1e-7}[planes]
     assert err < bound, err
 
 
@@ -123,17 +124,20 @@ def _golden(name):
 
 
 def test_forward_split_c4_d64_against_stored_oracle():
-    """Full-size split-precision solve (D_cut = 64, 30 steps, split from step 5)
-    against the oracle's stored ln Z / N (tests/golden/make_golden.py c4_d64_s0)."""
+    """Full-size split-precision solve in the benchmark's configuration
+    (D_cut = 64, 30 steps, FP64 steps 1-4, four bf16 planes on steps 5-6,
+    three after) against the oracle's stored ln Z / N
+    (tests/golden/make_golden.py c4_d64_s0): within the 1e-9 target."""
     g = _golden("c4_d64_s0")
     T0 = synth.random_symmetric_T0(0, 4)
-    with hot.Plan(4, 64, 30, "bf16x6", split_from_step=5, want_grad=False) as p:
+    with hot.Plan(4, 64, 30, "bf16x6", split_from_step=5, want_grad=False,
+                  hi_precision_steps=2) as p:
         lnz, ln, sign = p.forward_tensor(T0)
     err = abs(lnz - g["lnz"])
     print(f"c4 d64 bf16x6: |dlnz| = {err:.3e}")
     assert sign == g["trace_sign"]
     assert np.max(np.abs(ln[:4] - np.array(g["log_norms"][:4]))) < 1e-12   # FP64 steps
-    assert err < 1e-8
+    assert err < 1e-9
 
 
 @pytest.mark.parametrize("precision", ["bf16x6", "fp64"])
