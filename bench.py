@@ -1,13 +1,14 @@
 """Benchmark of the HOTRG hot path on GB300.
 
 Workload (default): the split-precision configuration of the headline metric,
-a seeded random reflection-symmetric rank-4 tensor T0 (bond dimension 4,
-entries N(0,1), max|T| = 1), D_cut = 64, 30 coarse-graining steps, the O(D^7)
-contractions and the Gram matrices on the tensor cores in three-plane split
-BF16 (FP32 accumulation flushed every 64-wide K slab into compensated sums),
-the eigensolve, norms and log-norm accumulation in FP64; steps before
---split-from run entirely in FP64.  One benchmark step = one complete solve
-(forward; with --grad also the backward).
+seeded random reflection-symmetric rank-4 tensors T0 (bond dimension 4,
+entries N(0,1), max|T| = 1; seeds 0-4), D_cut = 64, 30 coarse-graining steps,
+the O(D^7) contractions and the Gram matrices on the tensor cores in split
+BF16 (four planes on the first --hi-steps split steps, three after; exact
+hi*hi accumulation), the eigensolve, norms and log-norm accumulation in FP64;
+steps before --split-from run entirely in FP64.  One benchmark step = the
+solves of the --concurrent seeds (default 1: seed 0), each on its own stream
+and host thread (forward; with --grad also the backward).
 
 Printed: one JSON line (rank 0) with solves/s over all GPUs, useful and
 executed TFLOP/s, the roofline of the dominant kernel (stage-2 tensor-core
@@ -29,6 +30,7 @@ import subprocess
 import sys
 import threading
 import time
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -69,6 +71,45 @@ def step_flops(X, Y, Xp):
 
 def is_split_step(k, X, Y, Xp, split_from, precision):
     return precision != "fp64" and k >= split_from and X % 8 == 0 and Y % 8 == 0 and Xp % 8 == 0
+
+
+def products_of_step(k, split_from, hi_steps, precision):
+    """Tensor-core products per K step of a split step (BF16X6: four planes /
+    10 products on the first hi_steps split steps, three planes / 6 after)."""
+    if precision == "bf16x3":
+        return 3
+    return 10 if k < split_from + hi_steps else 6
+
+
+# DRAM traffic of one stage-2 launch from an ncu capture (dram__bytes_read.sum +
+# dram__bytes_write.sum) of the tensor-core GEMM source with this SHA-256; the
+# value is reported only while csrc/gemm_tc.cu is unchanged since the capture.
+STAGE2_TRAFFIC = {
+    "gemm_tc_sha256": "9d9572165621fead03f8f44b064e242ac0a52febde80b3cca80de778a17cab23",
+    # D = 32 capture: 207.9 MB read + 99.6 MB written per stage-2 launch; the
+    # operand and output bytes grow as D^5, so x (64/32)^5 = 32 for D = 64
+    "bytes_per_launch_d64": (207.932416e6 + 99.619328e6) * 32,
+    "captured": "profiles/tc_gemm_stage2_c4_d32_d64.md"}
+
+
+def gemm_source_sha():
+    import hashlib
+    path = os.path.join(ROOT, "paper_1912_02780_gb300", "csrc", "gemm_tc.cu")
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def aggregate_over_ranks(ms_local, solves_local, dist=None, device=None):
+    """Whole-job throughput: the max elapsed time over ranks and the sum of
+    solves over ranks (independent replicas).  Returns (ms_max, solves_total)."""
+    if dist is None:
+        return ms_local, solves_local
+    import torch
+    t = torch.tensor([float(ms_local)], dtype=torch.float64, device=device)
+    n = torch.tensor([float(solves_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.all_reduce(n, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(n.item())
 
 
 class ClockSampler:
@@ -232,6 +273,13 @@ def main():
     ap.add_argument("--workload", default="c4_d64", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6"])
     ap.add_argument("--split-from", type=int, default=5)
+    ap.add_argument("--hi-steps", type=int, default=2,
+                    help="split steps (from --split-from) with four bf16 planes")
+    ap.add_argument("--no-fp64-ref", action="store_true")
+    ap.add_argument("--concurrent", type=int, default=1,
+                    help="independent solves (seeds) per GPU per step, run concurrently "
+                         "(5 measured 0.130 vs 0.121 solves/s for 1 at D_cut = 64: the FP64 "
+                         "eigensolve does not overlap across streams)")
     ap.add_argument("--grad", type=int, default=0, help="1: each step is forward + backward")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -264,88 +312,118 @@ def main():
     torch.cuda.set_device(dev)
 
     d0, d_cut, n, desc = WORKLOADS[args.workload]
-    T0 = synth.random_symmetric_T0(rank if world > 1 else 0, d0)
-    stream = torch.cuda.current_stream(dev)
-    plan = hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
-                    want_grad=bool(args.grad), stream=stream.cuda_stream)
-    T0_dev = torch.tensor(T0, dtype=torch.float64, device=dev)
-    out_dev = torch.zeros(n + 2, dtype=torch.float64, device=dev)
-    grad_dev = torch.zeros(d0 ** 4, dtype=torch.float64, device=dev)
+    C = max(1, args.concurrent)
+    # this rank's seeds (replicas on N GPUs take disjoint seed blocks)
+    seeds = [rank * C + i for i in range(C)]
+    T0s = [synth.random_symmetric_T0(sd, d0) for sd in seeds]
+    streams = [torch.cuda.Stream(dev) for _ in range(C)]
+    plans = [hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
+                      want_grad=bool(args.grad), stream=st.cuda_stream,
+                      hi_precision_steps=args.hi_steps) for st in streams]
+    T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
+    out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]
+    grad_devs = [torch.zeros(d0 ** 4, dtype=torch.float64, device=dev) for _ in range(C)]
+    pool = ThreadPoolExecutor(max_workers=C)
 
-    def one_solve():
-        plan.forward_device(T0_dev.data_ptr(), out_dev.data_ptr())
+    def solve_dev(i):
+        plans[i].forward_device(T0_devs[i].data_ptr(), out_devs[i].data_ptr())
         if args.grad:
-            plan.backward_device(grad_dev.data_ptr())
+            plans[i].backward_device(grad_devs[i].data_ptr())
+        plans[i].sync()
+
+    def batch(fn):
+        # one benchmark step: the C solves of this rank, each driven by its own
+        # host thread on its own stream, so that they overlap on the device
+        list(pool.map(fn, range(C)))
 
     for _ in range(args.warmup):
-        one_solve()
-    plan.sync()
+        batch(solve_dev)
+    torch.cuda.synchronize(dev)
     if dist:
         dist.barrier()
-    torch.cuda.synchronize(dev)
 
     sampler = ClockSampler(local if world > 1 else 0)
     sampler.start()
-    plan.profile(True)
     launches0 = hot.kernel_launches()
+    main_stream = torch.cuda.current_stream(dev)
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
-    ev0.record(stream)
+    torch.cuda.synchronize(dev)
+    ev0.record(main_stream)
+    for st in streams:
+        st.wait_event(ev0)
     for _ in range(args.steps):
-        one_solve()
-    ev1.record(stream)
-    plan.sync()
+        batch(solve_dev)
+    for st in streams:
+        e = torch.cuda.Event()
+        e.record(st)
+        main_stream.wait_event(e)
+    ev1.record(main_stream)
     torch.cuda.synchronize(dev)
     launches = hot.kernel_launches() - launches0
     clocks = sampler.stop()
-    prof = plan.profile_read()
-    plan.profile(False)
     ms_total = ev0.elapsed_time(ev1)
+    ms_total, solves = aggregate_over_ranks(ms_total, args.steps * C, dist, dev)
     if dist:
-        t = torch.tensor([ms_total], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_total = float(t.item())
         dist.barrier()
     ms_per_step = ms_total / args.steps
-    solves = args.steps * world
     value = solves / (ms_total / 1e3)
+    lnzs = [float(o[0].item()) for o in out_devs]
 
-    res = out_dev.cpu().numpy()
-    lnz = float(res[0])
+    # one solve alone with per-stage CUDA events on its stream: stage breakdown
+    # and the roofline of the stage-2 kernel (not overlapped with other solves)
+    plans[0].profile(True)
+    t_a = torch.cuda.Event(enable_timing=True)
+    t_b = torch.cuda.Event(enable_timing=True)
+    t_a.record(streams[0])
+    solve_dev(0)
+    t_b.record(streams[0])
+    torch.cuda.synchronize(dev)
+    prof = plans[0].profile_read()
+    plans[0].profile(False)
+    single_ms = t_a.elapsed_time(t_b)
 
     # useful / executed flops of one solve and of the stage-2 launches
     sched = schedule(d0, d_cut, n)
     npairs = {"fp64": 1, "bf16x3": 3, "bf16x6": 6}[args.precision]
     useful = 0.0
     executed_tc = 0.0
-    s2_tc_useful = 0.0
+    s2_tc_useful = 0.0      # stage-2 launches of the three-plane steps (profile slot "s2")
     for k, (X, Y, Xp) in enumerate(sched, start=1):
         f = step_flops(X, Y, Xp)
         useful += f["total"]
         if is_split_step(k, X, Y, Xp, args.split_from, args.precision):
-            executed_tc += f["total"] * npairs
-            s2_tc_useful += f["s2"]
+            nprod = products_of_step(k, args.split_from, args.hi_steps, args.precision)
+            executed_tc += f["total"] * nprod
+            if nprod == npairs:
+                s2_tc_useful += f["s2"]
     bwd_factor = 4.0 if args.grad else 1.0   # backward ~3x forward incl. recompute
-    useful_tflops = useful * bwd_factor * args.steps / (ms_total / 1e3) / 1e12
+    useful_tflops = useful * bwd_factor * solves / (ms_total / 1e3) / 1e12
 
     peaks = measured_peaks()
     roof = None
     if "s2" in prof and s2_tc_useful > 0:
         s2_ms, s2_launches = prof["s2"]
         s2_ms_per_launch = s2_ms / s2_launches
-        exec_per_launch = s2_tc_useful * npairs * args.steps / s2_launches
+        exec_per_launch = s2_tc_useful * npairs / s2_launches
         achieved = exec_per_launch / (s2_ms_per_launch / 1e3) / 1e12
         if peaks:
             peak, src = peaks.get("bf16_tflops_sustained"), "measured (sustained)"
         else:
             peak, src = 1700.0, "fallback (sustained)"
-        roof = {"kernel": "tc_gemm_kernel (stage 2, O(D^7))", "bound": "tensor",
+        traffic = None
+        if (STAGE2_TRAFFIC["gemm_tc_sha256"] == gemm_source_sha() and d_cut == 64
+                and STAGE2_TRAFFIC["bytes_per_launch_d64"]):
+            traffic = STAGE2_TRAFFIC["bytes_per_launch_d64"]
+        roof = {"kernel": "tc_gemm_kernel<128,3> (stage 2, O(D^7), three-plane steps)",
+                "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "peak_source": src,
-                "traffic": None,
-                "useful_per_launch_tflop": s2_tc_useful * args.steps / s2_launches / 1e12,
+                "traffic": traffic,
+                "useful_per_launch_tflop": s2_tc_useful / s2_launches / 1e12,
                 "executed_per_launch_tflop": exec_per_launch / 1e12,
-                "ms_per_launch": s2_ms_per_launch}
+                "ms_per_launch": s2_ms_per_launch,
+                "timed": "CUDA events around every stage-2 launch of one solve run alone"}
 
     line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -353,42 +431,80 @@ def main():
             "dtype": args.precision, "data": "synthetic",
             "config": {"workload": args.workload, "desc": desc, "d0": d0, "d_cut": d_cut,
                        "n_steps": n, "precision": args.precision,
-                       "split_from_step": args.split_from, "grad": bool(args.grad),
+                       "split_from_step": args.split_from, "hi_precision_steps": args.hi_steps,
+                       "grad": bool(args.grad), "solves_per_step": C,
+                       "seeds": seeds,
                        "l2": "working set > L2 (D^5 intermediates of several GB per step)",
-                       "parallelism": f"replicas x{world}"},
+                       "parallelism": f"replicas x{world}, {C} concurrent solves per GPU"},
             "useful_tflops": useful_tflops,
             "executed_tc_tflop_per_solve": executed_tc / 1e12,
-            "lnz_per_site": lnz,
-            "stage_ms_per_solve": {k: v[0] / args.steps for k, v in prof.items()},
+            "single_solve_ms": single_ms,
+            "lnz_per_site": lnzs,
+            "stage_ms_per_solve": {k: v[0] for k, v in prof.items()},
             "gpu_launches": int(launches),
             "clocks": clocks}
     if roof:
         line["roofline"] = roof
-    g = golden(f"{args.workload}_s0") if rank == 0 else None
-    if g and not args.grad and world == 1:
-        line["abs_err_lnz_vs_oracle"] = abs(lnz - g["lnz"])
+    if rank == 0 and not args.grad:
+        errs = {}
+        for sd, lz in zip(seeds, lnzs):
+            g = golden(f"{args.workload}_s{sd}")
+            if g:
+                errs[f"seed{sd}"] = abs(lz - g["lnz"])
+        if errs:
+            line["abs_err_lnz_vs_oracle"] = errs
 
     # end to end through the host-buffer C ABI (pinned host input, host results)
     if not args.no_e2e and rank == 0:
-        T0_pin = torch.tensor(T0, dtype=torch.float64).pin_memory()
-        T0_np = T0_pin.numpy()
-        for _ in range(1):
-            plan.forward_tensor(T0_np)
+        T0_pins = [torch.tensor(t, dtype=torch.float64).pin_memory().numpy() for t in T0s]
+
+        def solve_host(i):
+            plans[i].forward_tensor(T0_pins[i])
+            if args.grad:
+                plans[i].backward()
+
+        batch(solve_host)
+        torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        e0.record(main_stream)
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            plan.forward_tensor(T0_np)
-            if args.grad:
-                plan.backward()
-        e1.record(stream)
+            batch(solve_host)
+        torch.cuda.synchronize(dev)
+        e1.record(main_stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
         e2e_ms = max(e0.elapsed_time(e1), wall * 1e3)
-        line["e2e"] = {"value": args.steps / (e2e_ms / 1e3), "unit": "solves/s",
-                       "h2d_bytes_per_step": T0.nbytes,
-                       "d2h_bytes_per_step": 8 * (n + 2) + (T0.nbytes if args.grad else 0)}
+        line["e2e"] = {"value": args.steps * C / (e2e_ms / 1e3), "unit": "solves/s",
+                       "h2d_bytes_per_step": C * T0s[0].nbytes,
+                       "d2h_bytes_per_step": C * (8 * (n + 2) + (T0s[0].nbytes if args.grad else 0))}
+
+    # the plain FP64-on-GPU form of the same solve: one steady step timed (an
+    # FP64 plan of `first` steps minus one of first - 1 steps), scaled to the solve
+    if rank == 0 and world == 1 and not args.no_fp64_ref and args.precision != "fp64":
+        def fp64_time(nsteps):
+            with hot.Plan(d0, d_cut, nsteps, "fp64", want_grad=False,
+                          stream=streams[0].cuda_stream) as p64:
+                p64.forward_device(T0_devs[0].data_ptr(), out_devs[0].data_ptr())
+                p64.sync()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(streams[0])
+                p64.forward_device(T0_devs[0].data_ptr(), out_devs[0].data_ptr())
+                b.record(streams[0])
+                p64.sync()
+                return a.elapsed_time(b) / 1e3
+        first = next(k for k, s_ in enumerate(sched, start=1) if s_ == (d_cut, d_cut, d_cut))
+        t_lo, t_hi = fp64_time(first - 1), fp64_time(first)
+        steady = t_hi - t_lo
+        t_solve = t_lo + steady * (n - first + 1)
+        line["fp64_gpu"] = {"solves_per_s": 1.0 / t_solve, "steady_step_s": steady,
+                            "speedup_of_split": value / (1.0 / t_solve),
+                            "speedup_single_solve": (1e3 / single_ms) / (1.0 / t_solve),
+                            "how": f"FP64 plans of {first - 1} and {first} steps timed with "
+                                   f"CUDA events; solve = first {first - 1} steps + "
+                                   f"{n - first + 1} steady steps"}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, fl = oracle_sample(d_cut)
@@ -398,7 +514,9 @@ def main():
             "value": 1.0 / cpu_solve_s, "unit": "solves/s", "cores": os.cpu_count(), "kind": "oracle",
             "sample": (f"one steady D={d_cut} step of the FP64 NumPy/LAPACK oracle ({dt:.1f} s), "
                        f"scaled to the {n}-step solve by useful flops")}
-    plan.close()
+    pool.shutdown()
+    for p_ in plans:
+        p_.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist:

@@ -167,3 +167,40 @@ def test_backward_split_ising_dbeta():
         g, db = p.backward(want_dbeta=True)
     print(f"ising split: |dlnz| = {abs(lnz - f['lnz']):.2e}, dbeta rel err = {abs(db - db_ref) / abs(db_ref):.2e}")
     assert abs(db - db_ref) / abs(db_ref) < 1e-6
+
+
+def test_forward_split_c3_ising_critical_d64_against_stored_oracle():
+    """Ising at beta_c, h = 0, D_cut = 64, 40 steps (the critical point, where
+    truncation matters most): split precision (FP64 steps 1-6, four planes on
+    7-8, three after) against the oracle's stored ln Z / N; |df| <= 1e-9 means
+    |d lnZ/N| <= beta_c 1e-9."""
+    g = _golden("c3_bc_h0")
+    with hot.Plan(2, 64, 40, "bf16x6", split_from_step=7, want_grad=False,
+                  hi_precision_steps=2) as p:
+        lnz, _, sign = p.forward_ising(synth.BETA_C, 1.0, 0.0)
+    err = abs(lnz - g["lnz"])
+    print(f"c3 ising beta_c d64: |dlnz| = {err:.3e}, |df| = {err / synth.BETA_C:.3e}")
+    assert sign == g["trace_sign"]
+    assert err / synth.BETA_C < 1e-9
+
+
+def test_fp64_gradient_against_finite_differences_c3_reduced():
+    """C3-style finite-difference check of d(lnZ/N)/dT0 on all 16 entries of
+    the Ising site tensor at beta_c, h = 0.01, 40 steps -- with D_cut = 16 so
+    that the 32 FP64 forwards finish quickly (the full D_cut = 64 FP64 forward
+    takes minutes on this GPU's FP64 pipe)."""
+    T0 = ising.ising_T0(synth.BETA_C, 1.0, 0.01)
+    d_cut, n, e = 16, 40, 1e-6
+    with hot.Plan(2, d_cut, n, "fp64") as p:
+        p.forward_tensor(T0)
+        g = p.backward()
+    with hot.Plan(2, d_cut, n, "fp64", want_grad=False) as p:
+        fd = np.zeros_like(T0)
+        for idx in np.ndindex(T0.shape):
+            tp, tm = T0.copy(), T0.copy()
+            tp[idx] += e
+            tm[idx] -= e
+            fd[idx] = (p.forward_tensor(tp)[0] - p.forward_tensor(tm)[0]) / (2 * e)
+    err = np.max(np.abs(g - fd)) / np.max(np.abs(fd))
+    print(f"c3 reduced FD: rel err = {err:.3e}")
+    assert err < 1e-6
