@@ -5,7 +5,9 @@ seeded random reflection-symmetric rank-4 tensors T0 (bond dimension 4,
 entries N(0,1), max|T| = 1; seeds 0-4), D_cut = 64, 30 coarse-graining steps,
 the O(D^7) contractions and the Gram matrices on the tensor cores in split
 BF16 (four planes on the first --hi-steps split steps, three after; exact
-hi*hi accumulation), the eigensolve, norms and log-norm accumulation in FP64;
+hi*hi accumulation), the eigensolve (randomized subspace iteration with
+Rayleigh-Ritz, or cuSOLVER's partial solver), norms and log-norm accumulation
+in FP64;
 steps before --split-from run entirely in FP64.  One benchmark step = the
 solves of the --concurrent seeds (default 1: seed 0), each on its own stream
 and host thread (forward; with --grad also the backward).
@@ -276,6 +278,9 @@ def main():
     ap.add_argument("--hi-steps", type=int, default=2,
                     help="split steps (from --split-from) with four bf16 planes")
     ap.add_argument("--no-fp64-ref", action="store_true")
+    ap.add_argument("--eigh-mode", type=int, default=1,
+                    help="0: cuSOLVER partial eigensolve; 1: randomized subspace eigensolver")
+    ap.add_argument("--power-iters", type=int, default=3)
     ap.add_argument("--concurrent", type=int, default=1,
                     help="independent solves (seeds) per GPU per step, run concurrently "
                          "(5 measured 0.130 vs 0.121 solves/s for 1 at D_cut = 64: the FP64 "
@@ -319,7 +324,8 @@ def main():
     streams = [torch.cuda.Stream(dev) for _ in range(C)]
     plans = [hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
                       want_grad=bool(args.grad), stream=st.cuda_stream,
-                      hi_precision_steps=args.hi_steps) for st in streams]
+                      hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
+                      eigh_power_iters=args.power_iters) for st in streams]
     T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
     out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]
     grad_devs = [torch.zeros(d0 ** 4, dtype=torch.float64, device=dev) for _ in range(C)]
@@ -432,6 +438,8 @@ def main():
             "config": {"workload": args.workload, "desc": desc, "d0": d0, "d_cut": d_cut,
                        "n_steps": n, "precision": args.precision,
                        "split_from_step": args.split_from, "hi_precision_steps": args.hi_steps,
+                       "eigh": ("randomized subspace, %d power iterations" % args.power_iters
+                                if args.eigh_mode == 1 else "cuSOLVER syevdx (top D'+1)"),
                        "grad": bool(args.grad), "solves_per_step": C,
                        "seeds": seeds,
                        "l2": "working set > L2 (D^5 intermediates of several GB per step)",

@@ -87,13 +87,19 @@ typedef struct {
   int hi_precision_steps;   /* with HOTRG_BF16X6: the first hi_precision_steps split steps use
                                four bf16 planes (10 products, ~32 significant bits) instead of
                                three; these steps weigh most in ln Z / N (weight 2^-k)     */
+  int eigh_mode;            /* plans without gradients: 0 = cuSOLVER partial eigensolve of the
+                               D'+1 largest pairs; 1 = randomized subspace eigensolver (FP64
+                               block power iteration on 4 D' vectors with Householder QR,
+                               then Rayleigh-Ritz; used where 4 D' < X^2).  Plans with
+                               gradients always take all eigenpairs.                      */
+  int eigh_power_iters;     /* power iterations of eigh_mode 1 (<= 0: 4)                   */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
 
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
- * hi_precision_steps = 2.
+ * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
@@ -207,8 +213,9 @@ void hotrg_server_destroy(hotrg_server server);
  * Slots: 0 Gram, 1 eigensolve (+ sort/sign fix), 2 stage-1 contraction,
  * 3 stage-2 contraction (the O(D^7) GEMM), 4 stage-3 contraction, 5 norm,
  * 6 operand preparation (bf16 split), 7 backward contractions, 8 backward
- * eigensolve adjoint, 9 backward Gram adjoint; slot + 16 = the same stage run
- * by the FP64 GEMM instead of the tensor-core GEMM. */
+ * eigensolve adjoint, 9 backward Gram adjoint, 10 stage-2 contraction of the
+ * four-plane steps; slot + 16 = the same stage run by the FP64 GEMM instead of
+ * the tensor-core GEMM. */
 #define HOTRG_PROFILE_SLOTS 32
 hotrg_status hotrg_profile_enable(hotrg_plan plan, int enable);
 hotrg_status hotrg_profile_read(hotrg_plan plan, double* ms, int* counts);

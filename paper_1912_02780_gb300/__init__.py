@@ -39,7 +39,7 @@ EXPORTS = (
 )
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
-               7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj"}
+               7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj", 10: "s2_4plane"}
 
 
 class hotrg_config(ctypes.Structure):
@@ -47,7 +47,8 @@ class hotrg_config(ctypes.Structure):
                 ("precision", ctypes.c_int), ("split_from_step", ctypes.c_int),
                 ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
                 ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
-                ("hi_precision_steps", ctypes.c_int)]
+                ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
+                ("eigh_power_iters", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -141,7 +142,8 @@ def _p(a: np.ndarray):
 def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_step: int = 1,
                 want_grad: bool = True, fixed_w_grad: bool = False,
                 eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
-                hi_precision_steps: int = 2) -> hotrg_config:
+                hi_precision_steps: int = 2, eigh_mode: int = 0,
+                eigh_power_iters: int = 4) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -151,6 +153,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_broadening = eigh_broadening
     c.gram_split_from_step = gram_split_from_step
     c.hi_precision_steps = hi_precision_steps
+    c.eigh_mode = eigh_mode
+    c.eigh_power_iters = eigh_power_iters
     return c
 
 
@@ -174,10 +178,11 @@ class Plan:
     def __init__(self, d0: int, d_cut: int, n_steps: int, precision="fp64",
                  split_from_step: int = 1, want_grad: bool = True, fixed_w_grad: bool = False,
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
-                 gram_split_from_step: int = 0, hi_precision_steps: int = 2):
+                 gram_split_from_step: int = 0, hi_precision_steps: int = 2,
+                 eigh_mode: int = 0, eigh_power_iters: int = 4):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
-                               hi_precision_steps)
+                               hi_precision_steps, eigh_mode, eigh_power_iters)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

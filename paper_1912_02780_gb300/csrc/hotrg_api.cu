@@ -20,6 +20,7 @@
 // the adjoint of w, plus the adjoint of the truncated eigensolve and of the
 // Gram assembly) recomputes U and V per step from the stored T_k and w_k.
 #include <cusolverDn.h>
+#include <algorithm>
 #include <atomic>
 #include <cmath>
 #include <cstdio>
@@ -155,6 +156,10 @@ struct hotrg_plan_s {
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
   double* F64 = nullptr;  // same, FP64, for the four-plane steps
   double* splitk = nullptr;   // FP64 split-K partials (deterministic reduction)
+  // randomized subspace eigensolver (eigh_mode 1)
+  double *Qs = nullptr, *Zs = nullptr, *Hs = nullptr, *tau = nullptr, *swork = nullptr,
+         *wsmall = nullptr;
+  int kspace = 0, lswork = 0;
   bool have_fwd = false, fwd_ising = false;
   std::string last_error;
   // optional per-stage CUDA-event timing
@@ -238,6 +243,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->d0 < 1 || c->d_cut < 1 || c->n_steps < 1 || c->n_steps > 200) return HOTRG_EINVAL;
   if (c->precision < HOTRG_FP64 || c->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
   if (c->split_from_step < 1 || c->hi_precision_steps < 0) return HOTRG_EINVAL;
+  if (c->eigh_mode < 0 || c->eigh_mode > 1) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -312,7 +318,8 @@ TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long 
 // ---- forward pieces -------------------------------------------------------
 
 enum StageId { kStGram = 0, kStEigh = 1, kStS1 = 2, kStS2 = 3, kStS3 = 4, kStNorm = 5,
-               kStPrep = 6, kStBwdContract = 7, kStBwdEigh = 8, kStBwdGram = 9, kStF64 = 16 };
+               kStPrep = 6, kStBwdContract = 7, kStBwdEigh = 8, kStBwdGram = 9, kStS2Hi = 10,
+               kStF64 = 16 };
 
 hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* A, double* B,
                       double* G) {
@@ -425,7 +432,7 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     }
     const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
     {
-    Stage sc(p, kStS2);
+    Stage sc(p, np == 4 ? kStS2Hi : kStS2);
     CK(tc_gemm(u, pp,
                tcg(p, np, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
                    map2(X, 1, X2), stage_mode(np), stage_buf(p, np), 0),
@@ -447,6 +454,60 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
 
 double* E_of(hotrg_plan p, int k) { return p->cfg.want_grad ? p->E[k - 1] : p->E[0]; }
 
+bool use_subspace(const hotrg_plan p, const StepGeom& s) {
+  return p->cfg.eigh_mode == 1 && !p->cfg.want_grad && 4LL * s.Xp < s.N;
+}
+
+// Randomized subspace eigensolver for the leading eigenpairs of the symmetric
+// PSD Gram matrix G (N x N, in p->Escr): a block of k = 4 D' vectors, started
+// from a deterministic pseudo-random block, is multiplied by G eigh_power_iters
+// times with a Householder QR (cuSOLVER geqrf + orgqr) after each product, and
+// the Rayleigh-Ritz problem Q^T G Q (k x k, cuSOLVER syevd) gives the Ritz
+// pairs.  All in FP64.  The block is stored as k contiguous vectors of length
+// N, i.e. an N x k column-major matrix for cuSOLVER.  Output: the k Ritz
+// vectors (ascending Ritz values) in p->Zs as contiguous rows and the Ritz
+// values in p->wasc, ready for eig_desc.
+hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
+  cudaStream_t st = p->stream;
+  const int N = (int)s.N, K = 4 * s.Xp;
+  const int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
+  CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
+  for (int it = 0; it <= iters; ++it) {
+    if (it > 0) {
+      // Z = G Q (as rows: Z[a][i] = sum_j Q[a][j] G[i][j]), then Q = orth(Z)
+      CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Escr, map_lin(N), map_lin(1), p->Zs,
+                      map_lin(N), map_lin(1), K, N, N, 1.0, 0.0),
+                  st, p->sms));
+      CK(cudaMemcpyAsync(p->Qs, p->Zs, sizeof(double) * (size_t)K * N, cudaMemcpyDeviceToDevice,
+                         st));
+    }
+    if (cusolverDnDgeqrf(p->solver, N, K, p->Qs, N, p->tau, p->swork, p->lswork, p->info) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return fail(p, HOTRG_ECUDA, "cusolverDnDgeqrf failed");
+    CK(eigh_info_check(p->info, p->err, st));
+    if (cusolverDnDorgqr(p->solver, N, K, K, p->Qs, N, p->tau, p->swork, p->lswork, p->info) !=
+        CUSOLVER_STATUS_SUCCESS)
+      return fail(p, HOTRG_ECUDA, "cusolverDnDorgqr failed");
+    CK(eigh_info_check(p->info, p->err, st));
+  }
+  // Rayleigh-Ritz: Z = G Q, H[a][b] = sum_i Q[a][i] Z[b][i]
+  CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Escr, map_lin(N), map_lin(1), p->Zs,
+                  map_lin(N), map_lin(1), K, N, N, 1.0, 0.0),
+              st, p->sms));
+  CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Zs, map_lin(N), map_lin(1), p->Hs,
+                  map_lin(K), map_lin(1), K, K, N, 1.0, 0.0),
+              st, p->sms));
+  if (cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, K, p->Hs, K,
+                       p->wasc, p->swork, p->lswork, p->info) != CUSOLVER_STATUS_SUCCESS)
+    return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd (Rayleigh-Ritz) failed");
+  CK(eigh_info_check(p->info, p->err, st));
+  // Ritz vectors as rows: V[c][i] = sum_a S[a][c] Q[a][i]  (S column-major K x K)
+  CK(gemm_f64(g64(p, p->Hs, map_lin(K), map_lin(1), p->Qs, map_lin(1), map_lin(N), p->Zs,
+                  map_lin(N), map_lin(1), K, N, K, 1.0, 0.0),
+              st, p->sms));
+  return HOTRG_OK;
+}
+
 hotrg_status step_forward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
   cudaStream_t st = p->stream;
@@ -463,7 +524,13 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   Stage sc(p, kStEigh);
   CK(diag_trace(p->Escr, N, p->scal + 3, st));
   int ncols = N;
-  if (p->cfg.want_grad || s.Xp >= N) {
+  const double* evec = p->Escr;
+  if (use_subspace(p, s)) {
+    hotrg_status rr = eigh_subspace(p, s, k);
+    if (rr != HOTRG_OK) return rr;
+    ncols = 4 * s.Xp;
+    evec = p->Zs;
+  } else if (p->cfg.want_grad || s.Xp >= N) {
     // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
     cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
                                            CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc,
@@ -480,7 +547,7 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     ncols = s.Xp + 1;
   }
   CK(eigh_info_check(p->info, p->err, st));
-  CK(eig_desc(p->Escr, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
+  CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
   CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
   }
   if (s.split) r = contract_split(p, s, T, Ek, Tout);
@@ -717,6 +784,8 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_broadening = 1e-12;
   c->gram_split_from_step = 0;
   c->hi_precision_steps = 2;
+  c->eigh_mode = 0;
+  c->eigh_power_iters = 4;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -863,6 +932,34 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   }
   p->lwork = lw;
   ALC(p->work, (long long)lw);
+  if (cfg->eigh_mode == 1 && !cfg->want_grad) {
+    int kmax = 0;
+    long long nmax = 0;
+    for (const StepGeom& g : L.g)
+      if (4LL * g.Xp < g.N && 4 * g.Xp > kmax) kmax = 4 * g.Xp;
+    nmax = L.maxN;
+    if (kmax > 0) {
+      p->kspace = kmax;
+      ALC(p->Qs, nmax * kmax);
+      ALC(p->Zs, nmax * kmax);
+      ALC(p->Hs, (long long)kmax * kmax);
+      ALC(p->tau, kmax);
+      int l1 = 0, l2 = 0, l3 = 0, ls = 0;
+      for (const StepGeom& g : L.g) {
+        if (!(4LL * g.Xp < g.N)) continue;
+        const int Kq = 4 * g.Xp, Nq = (int)g.N;
+        if (cusolverDnDgeqrf_bufferSize(p->solver, Nq, Kq, p->Qs, Nq, &l1) != CUSOLVER_STATUS_SUCCESS ||
+            cusolverDnDorgqr_bufferSize(p->solver, Nq, Kq, Kq, p->Qs, Nq, p->tau, &l2) !=
+                CUSOLVER_STATUS_SUCCESS ||
+            cusolverDnDsyevd_bufferSize(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
+                                        Kq, p->Hs, Kq, p->wasc, &l3) != CUSOLVER_STATUS_SUCCESS)
+          return cleanup(HOTRG_ECUDA);
+        ls = std::max(ls, std::max(l1, std::max(l2, l3)));
+      }
+      p->lswork = ls;
+      ALC(p->swork, (long long)ls);
+    }
+  }
   if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
 #undef ALC
   *out = p;

@@ -368,6 +368,17 @@ __global__ void scale_exp_neg_kernel(double* __restrict__ x, long long n,
   for (long long i = gtid(); i < n; i += gstride()) x[i] *= f;
 }
 
+// Deterministic pseudo-random fill in [-1, 1) (SplitMix64 of the index).
+__global__ void fill_random_kernel(double* __restrict__ x, long long n, unsigned long long seed) {
+  for (long long i = gtid(); i < n; i += gstride()) {
+    unsigned long long z = seed + 0x9E3779B97F4A7C15ull * (unsigned long long)(i + 1);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z = z ^ (z >> 31);
+    x[i] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
 __global__ void dot16_kernel(const double* __restrict__ a, const double* __restrict__ b, int n,
                              double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -509,6 +520,12 @@ cudaError_t scale_copy(const double* x, double* y, long long n, double a, cudaSt
 cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream_t st, int sms) {
   count_launch();
   scale_exp_neg_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, n, logc);
+  return cudaGetLastError();
+}
+
+cudaError_t fill_random(double* x, long long n, unsigned long long seed, cudaStream_t st, int sms) {
+  count_launch();
+  fill_random_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, n, seed);
   return cudaGetLastError();
 }
 

@@ -38,6 +38,7 @@ cudaError_t symmetrize(double* G, int N, cudaStream_t st, int sms);
 cudaError_t scale_copy(const double* x, double* y, long long n, double a, cudaStream_t st, int sms);
 // x <- x * exp(-*logc)  (divide by a norm whose log lives on the device)
 cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream_t st, int sms);
+cudaError_t fill_random(double* x, long long n, unsigned long long seed, cudaStream_t st, int sms);
 cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st);
 
 }  // namespace hotrg

@@ -204,3 +204,39 @@ def test_fp64_gradient_against_finite_differences_c3_reduced():
     err = np.max(np.abs(g - fd)) / np.max(np.abs(fd))
     print(f"c3 reduced FD: rel err = {err:.3e}")
     assert err < 1e-6
+
+
+@pytest.mark.parametrize("iters", [2, 3])
+def test_subspace_eigensolver_c4_d64_against_stored_oracle(iters):
+    """Forward with the randomized subspace eigensolver (eigh_mode 1: block
+    power iteration on 4 D' vectors + Rayleigh-Ritz) in the benchmark's
+    configuration: still within 1e-9 of the oracle's ln Z / N."""
+    g = _golden("c4_d64_s0")
+    T0 = synth.random_symmetric_T0(0, 4)
+    with hot.Plan(4, 64, 30, "bf16x6", split_from_step=5, want_grad=False,
+                  hi_precision_steps=2, eigh_mode=1, eigh_power_iters=iters) as p:
+        lnz, _, sign = p.forward_tensor(T0)
+        tr, _, _ = p.diagnostics()
+    err = abs(lnz - g["lnz"])
+    print(f"subspace eigh iters={iters}: |dlnz| = {err:.3e}")
+    assert sign == g["trace_sign"]
+    assert err < 1e-9
+    assert np.max(np.abs(tr - np.array(g["trunc_err"]))) < 1e-7
+
+
+def test_subspace_eigensolver_c3_ising_critical():
+    g = _golden("c3_bc_h0")
+    with hot.Plan(2, 64, 40, "bf16x6", split_from_step=7, want_grad=False,
+                  hi_precision_steps=2, eigh_mode=1, eigh_power_iters=3) as p:
+        lnz, _, _ = p.forward_ising(synth.BETA_C, 1.0, 0.0)
+    err = abs(lnz - g["lnz"])
+    print(f"subspace eigh c3: |df| = {err / synth.BETA_C:.3e}")
+    assert err / synth.BETA_C < 1e-9
+
+
+def test_subspace_eigensolver_fp64_close_to_full():
+    T0 = synth.random_symmetric_T0(0, 4)
+    ref = hotrg.hotrg_forward(T0, 32, 16, keep=False)
+    with hot.Plan(4, 32, 16, "fp64", want_grad=False, eigh_mode=1, eigh_power_iters=6) as p:
+        lnz, ln, _ = p.forward_tensor(T0)
+    assert abs(lnz - ref["lnz"]) < 1e-10
