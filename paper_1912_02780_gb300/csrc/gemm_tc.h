@@ -31,6 +31,8 @@ struct TcGemm {
   long long c_lim;           // elements per output plane: stores at or beyond are skipped
                              // and flagged (kErrBounds)
   int* err;                  // device error word
+  int bk;                    // K slab per pipeline stage: 32 or 64 (0: 64 for two or three
+                             // planes, 32 for four)
 };
 
 // Set the products of a precision: all plane pairs (i, j) with

@@ -54,8 +54,8 @@ __global__ void gather_split_kernel(const double* __restrict__ src, long long sr
 template <typename SrcT>
 __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm,
                                   IMap km, int rows, int K, int seg, int nplanes, int gridded,
-                                  long long plane_stride, __nv_bfloat16* __restrict__ dst,
-                                  int* err) {
+                                  int contig, long long plane_stride,
+                                  __nv_bfloat16* __restrict__ dst, int* err) {
   const int lane = threadIdx.x & 31;
   const long long warp0 = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5;
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -63,21 +63,40 @@ __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_li
   const long long work = (long long)rows * nseg;
   for (long long w = warp0; w < work; w += nwarps) {
     const int r = (int)(w / nseg), sg = (int)(w % nseg);
-    const int k0 = sg * seg;
+    // lane handles the 4 consecutive elements k0 .. k0 + 3 of the segment
+    const int k0 = sg * seg + 4 * lane;
+    const bool active = 4 * lane < seg && k0 < K;   // K is a multiple of 8
     const long long roff = imap(rm, r);
     float v[4];
     double vd[4];
     float mx = 0.f;
+    if (active) {
+      const long long off0 = roff + imap(km, k0);
+      if (contig && off0 >= 0 && off0 + 3 < src_lim &&
+          (off0 & (sizeof(SrcT) == 4 ? 3 : 1)) == 0) {
+        if constexpr (sizeof(SrcT) == 4) {
+          const float4 q = *reinterpret_cast<const float4*>(src + off0);
+          vd[0] = q.x; vd[1] = q.y; vd[2] = q.z; vd[3] = q.w;
+        } else {
+          const double2 a = *reinterpret_cast<const double2*>(src + off0);
+          const double2 b = *reinterpret_cast<const double2*>(src + off0 + 2);
+          vd[0] = a.x; vd[1] = a.y; vd[2] = b.x; vd[3] = b.y;
+        }
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+          const long long off = roff + imap(km, k0 + i);
+          vd[i] = 0.0;
+          if (off >= 0 && off < src_lim) vd[i] = (double)src[off];
+          else atomicOr(err, kErrBounds);
+        }
+      }
+    } else {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) vd[i] = 0.0;
+    }
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int kk = lane + 32 * i;
-      const int k = k0 + kk;
-      vd[i] = 0.0;
-      if (kk < seg && k < K) {
-        const long long off = roff + imap(km, k);
-        if (off >= 0 && off < src_lim) vd[i] = (double)src[off];
-        else atomicOr(err, kErrBounds);
-      }
       v[i] = (float)vd[i];
       mx = fmaxf(mx, fabsf(v[i]));
     }
@@ -88,41 +107,38 @@ __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_li
     int e = 0;
     frexpf(mx, &e);
     const float g = (mx > 0.f) ? ldexpf(1.f, max(e - 8, -126)) : 1.f;
+    if (!active) continue;
+    __nv_bfloat16 b[4][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-      const int kk = lane + 32 * i;
-      const int k = k0 + kk;
-      if (kk < seg && k < K) {
-        const long long o = (long long)r * K + k;
-        __nv_bfloat16 b0;
-        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
-        else b0 = __double2bfloat16(vd[i]);
-        dst[o] = b0;
-        if (nplanes > 1) {
-          __nv_bfloat16 b1, b2, b3;
-          if constexpr (sizeof(SrcT) == 4) {
-            // float source: the remainders are exact in float
-            const float rem = v[i] - __bfloat162float(b0);
-            b1 = __float2bfloat16_rn(rem);
-            const float rem2 = rem - __bfloat162float(b1);
-            b2 = __float2bfloat16_rn(rem2);
-            b3 = __float2bfloat16_rn(rem2 - __bfloat162float(b2));
-          } else {
-            // double source: the first remainder as a float pair keeps the bits
-            // a float would drop (enough for four planes), the rest in float
-            const double remd = vd[i] - (double)__bfloat162float(b0);
-            const float rh = (float)remd;
-            const float rl = (float)(remd - (double)rh);
-            b1 = __float2bfloat16_rn(rh);
-            const float rem2 = (rh - __bfloat162float(b1)) + rl;
-            b2 = __float2bfloat16_rn(rem2);
-            b3 = __float2bfloat16_rn(rem2 - __bfloat162float(b2));
-          }
-          dst[plane_stride + o] = b1;
-          if (nplanes > 2) dst[2 * plane_stride + o] = b2;
-          if (nplanes > 3) dst[3 * plane_stride + o] = b3;
-        }
+      __nv_bfloat16 b0;
+      if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
+      else b0 = __double2bfloat16(vd[i]);
+      b[0][i] = b0;
+      if constexpr (sizeof(SrcT) == 4) {
+        // float source: the remainders are exact in float
+        const float rem = v[i] - __bfloat162float(b0);
+        b[1][i] = __float2bfloat16_rn(rem);
+        const float rem2 = rem - __bfloat162float(b[1][i]);
+        b[2][i] = __float2bfloat16_rn(rem2);
+        b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
+      } else {
+        // double source: the first remainder as a float pair keeps the bits a
+        // float would drop (enough for four planes), the rest in float
+        const double remd = vd[i] - (double)__bfloat162float(b0);
+        const float rh = (float)remd;
+        const float rl = (float)(remd - (double)rh);
+        b[1][i] = __float2bfloat16_rn(rh);
+        const float rem2 = (rh - __bfloat162float(b[1][i])) + rl;
+        b[2][i] = __float2bfloat16_rn(rem2);
+        b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
       }
+    }
+    const long long o = (long long)r * K + k0;   // multiple of 4: 8-byte aligned
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q >= nplanes) break;
+      *reinterpret_cast<uint2*>(dst + q * plane_stride + o) = *reinterpret_cast<const uint2*>(b[q]);
     }
   }
 }
@@ -409,7 +425,10 @@ cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, i
   // Plane 0 on the grid only for three planes; with two planes a floating
   // plane 0 keeps more bits for small elements (see the comment above).
   const int gridded = nplanes >= 3 ? 1 : 0;
-  if (nplanes < 1 || nplanes > 4) return cudaErrorInvalidValue;
+  if (nplanes < 1 || nplanes > 4 || K % 8 != 0 || plane_stride % 4 != 0)
+    return cudaErrorInvalidValue;
+  // contiguous K (single-level unit-stride map): vector loads
+  const int contig = (km.s0 == 1 && km.r0 >= K) ? 1 : 0;
   const int seg = K < kGridSeg ? K : kGridSeg;
   const long long work = (long long)rows * ((K + seg - 1) / seg);
   if (work == 0) return cudaSuccess;
@@ -418,7 +437,7 @@ cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, i
   if (blocks > 32LL * sms) blocks = 32LL * sms;
   count_launch();
   grid_split_kernel<SrcT><<<(int)blocks, 256, 0, st>>>(src, src_lim, rm, km, rows, K, seg, nplanes,
-                                                        gridded, plane_stride, dst, err);
+                                                        gridded, contig, plane_stride, dst, err);
   return cudaGetLastError();
 }
 
