@@ -280,7 +280,7 @@ def main():
     ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--eigh-mode", type=int, default=1,
                     help="0: cuSOLVER partial eigensolve; 1: randomized subspace eigensolver")
-    ap.add_argument("--power-iters", type=int, default=3)
+    ap.add_argument("--power-iters", type=int, default=2)
     ap.add_argument("--concurrent", type=int, default=1,
                     help="independent solves (seeds) per GPU per step, run concurrently "
                          "(5 measured 0.130 vs 0.121 solves/s for 1 at D_cut = 64: the FP64 "

@@ -578,18 +578,37 @@ hotrg_status run_forward(hotrg_plan p) {
 // both operands from their FP64 sources through the same index maps, FP64
 // output, optional accumulation) when the step runs split and the operands fit
 // the plane buffers, else on the FP64 GEMM.
-cudaError_t run_gemm(hotrg_plan p, int np, const GemmF64& g) {
+// f32 flags: bit 0 / 1 / 2 = A / B / C is an FP32 staging buffer (passed as a
+// double pointer), which only the tensor-core path can read or write.
+enum : unsigned { kA32 = 1, kB32 = 2, kC32 = 4 };
+
+cudaError_t run_gemm(hotrg_plan p, int np, const GemmF64& g, unsigned f32 = 0) {
   const bool split = np > 0;
   const long long cap = p->L.chunkS;
   const bool ok = split && p->L.any_split && g.K % 8 == 0 && (g.beta == 0.0 || g.beta == 1.0) &&
                   (long long)g.M * g.K <= cap && (long long)g.N * g.K <= cap && g.K > 0;
-  if (!ok) return gemm_f64(g, p->stream, p->sms);
-  cudaError_t e = grid_split(g.A, g.a_lim, g.am, g.ak, g.M, g.K, np, cap, p->pU, p->err,
-                             p->stream, p->sms);
+  if (!ok) {
+    if (f32) return cudaErrorInvalidValue;   // FP32 staging needs the tensor-core path
+    return gemm_f64(g, p->stream, p->sms);
+  }
+  cudaError_t e;
+  if (f32 & kA32) {
+    const float* a = reinterpret_cast<const float*>(g.A);
+    e = grid_split(a, lim_of(p, a, sizeof(float)), g.am, g.ak, g.M, g.K, np, cap, p->pU, p->err,
+                   p->stream, p->sms);
+  } else {
+    e = grid_split(g.A, g.a_lim, g.am, g.ak, g.M, g.K, np, cap, p->pU, p->err, p->stream, p->sms);
+  }
   if (e != cudaSuccess) return e;
-  e = grid_split(g.B, g.b_lim, g.bn, g.bk, g.N, g.K, np, cap, p->pV, p->err, p->stream, p->sms);
+  if (f32 & kB32) {
+    const float* b = reinterpret_cast<const float*>(g.B);
+    e = grid_split(b, lim_of(p, b, sizeof(float)), g.bn, g.bk, g.N, g.K, np, cap, p->pV, p->err,
+                   p->stream, p->sms);
+  } else {
+    e = grid_split(g.B, g.b_lim, g.bn, g.bk, g.N, g.K, np, cap, p->pV, p->err, p->stream, p->sms);
+  }
   if (e != cudaSuccess) return e;
-  TcGemm t = tcg(p, np, g.M, g.N, g.K, g.cm, g.cn, kOutF64, g.C, 0);
+  TcGemm t = tcg(p, np, g.M, g.N, g.K, g.cm, g.cn, (f32 & kC32) ? kOutF32 : kOutF64, g.C, 0);
   t.alpha = (float)g.alpha;
   t.accumulate = g.beta != 0.0 ? 1 : 0;
   return tc_gemm(opnd(p->pU, g.M, g.K, np, cap), opnd(p->pV, g.N, g.K, np, cap), t, p->stream,
@@ -600,6 +619,9 @@ hotrg_status step_backward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
   const bool sp = s.split;
   const int snp = s.np;
+  // three-plane steps keep the D^5 intermediates U, V, P, Q in FP32 (they are
+  // split into 24 bits anyway); FP64 steps and four-plane steps keep FP64
+  const unsigned f = (snp == 3) ? 1u : 0u;
   const int X = s.X, Y = s.Y, Xp = s.Xp;
   const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
   const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X, YXp2 = (long long)Y * Xp2;
@@ -620,33 +642,33 @@ hotrg_status step_backward(hotrg_plan p, int k) {
     // recompute U and V of this chunk (as in the forward)
     CK(run_gemm(p, snp, g64(p, Ek, map2(X, 1, N), map_lin(X), Ty, map3(Y, X, 1, Y2, Y), map_lin(XY2), p->Ub,
                     map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY), Xp * X, yc * X * Y, X,
-                    1.0, 0.0)));
+                    1.0, 0.0), f * kC32));
     CK(run_gemm(p, snp, g64(p, p->Ub, map_lin(XY), map_lin(1), T, map2(X, Y2, 1), map2(Y, Y, XY2), p->Vb,
                     map3(Xp, X, Y * X2, X, Xp * Y * X2), map2(X, 1, X2), yc * X * Xp, Y * X,
-                    X * Y, 1.0, 0.0)));
+                    X * Y, 1.0, 0.0), f * (kA32 | kC32)));
     // P[(y a i)][(k z)] = sum_b Tbar'[a b y z] w[i k b]
     CK(run_gemm(p, snp, g64(p, Eby, map3(Y, Xp, Xp2, Xp, YXp2), map_lin(1), Ek, map_lin(1), map_lin(N),
                     p->Pb, map3(Y, Xp, 1, X2 * Y, (long long)Xp * X2 * Y), map2(X, Y, XY),
-                    yc * Xp * Y, X * X, Xp, 1.0, 0.0)));
+                    yc * Xp * Y, X * X, Xp, 1.0, 0.0), f * kC32));
     // Q[(y a i)][(b j)] = sum_{k z} P T[b k j z]
     CK(run_gemm(p, snp, g64(p, p->Pb, map_lin(XY), map_lin(1), T, map2(Y, Y, XY2), map2(Y, 1, Y2), p->Qb,
-                    map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0)));
+                    map_lin(XY), map_lin(1), yc * Xp * X, X * Y, X * Y, 1.0, 0.0), f * (kA32 | kC32)));
     // upper copy: Tbar[a i y j] += sum_{A b} w[a b A] Q[y A i b j]
     CK(run_gemm(p, snp, g64(p, Ek, map_lin(X), map2(X, 1, N), p->Qb, map3(Y, X, 1, XY, (long long)Xp * X * XY),
                     map2(X, Y, X * XY), p->Tbar + (long long)y0 * Y, map_lin(XY2),
-                    map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0)));
+                    map3(Y, X, 1, Y2, Y), X, yc * X * Y, Xp * X, 1.0, 1.0), f * kB32));
     // lower copy: Tbar[b k j z] += sum_{y i A} U[y i A b j] P[y A z i k]
     CK(run_gemm(p, snp, g64(p, p->Ub, map2(Y, 1, Y), map3(Xp, X, XY, Xp * XY, (long long)X * Xp * XY), p->Pb,
                     map2(Y, 1, Y), map3(Xp, X, X * XY, XY, (long long)Xp * X * XY), p->Tbar,
-                    map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0)));
+                    map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, yc * X * Xp, 1.0, 1.0), f * (kA32 | kB32)));
     // w carrying alpha: wbT[A][(a b)] += sum_{y i j} T[a i y j] Q[y A i b j]
     CK(run_gemm(p, snp, g64(p, Ty, map_lin(XY2), map3(Y, X, 1, Y2, Y), p->Qb, map2(X, Y, X * XY),
                     map3(Y, X, 1, XY, (long long)Xp * X * XY), p->wbT, map_lin(X), map2(X, 1, N),
-                    X, Xp * X, yc * X * Y, 1.0, 1.0)));
+                    X, Xp * X, yc * X * Y, 1.0, 1.0), f * kB32));
     // w carrying beta: wbT[B][(i k)] += sum_{y A z} V[y A z][(i k)] Tbar'[A B y z]
     CK(run_gemm(p, snp, g64(p, p->Vb, map_lin(1), map3(Y, Xp, X2, Y * X2, (long long)Xp * Y * X2), Eby,
                     map_lin(1), map3(Y, Xp, Xp2, Xp, YXp2), p->wbT, map_lin(1), map_lin(N),
-                    X * X, Xp, yc * Xp * Y, 1.0, 1.0)));
+                    X * X, Xp, yc * Xp * Y, 1.0, 1.0), f * kA32));
   }
   }
   if (!p->cfg.fixed_w_grad && Xp < N) {
