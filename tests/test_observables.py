@@ -1,0 +1,48 @@
+"""Host-side finite differences used for the specific heat (CPU) and the
+GPU thermodynamics on a beta grid against the oracle's stored values."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import exact
+
+
+def test_grid_derivative_is_second_order_exact_on_quadratics():
+    from paper_1912_02780_gb300.observables import grid_derivative
+    x = np.linspace(0.3, 0.6, 11)
+    y = 3 * x ** 2 - 2 * x + 1
+    assert np.max(np.abs(grid_derivative(x, y) - (6 * x - 2))) < 1e-12
+
+
+def test_grid_derivative_matches_onsager_energy_derivative():
+    # u = -d(lnZ/N)/dbeta of Onsager's closed form, differentiated on a fine grid
+    from paper_1912_02780_gb300.observables import grid_derivative
+    b = np.linspace(0.30, 0.36, 13)
+    lnz = np.array([exact.onsager_lnz_1d(x) for x in b])
+    d = grid_derivative(b, lnz)
+    e = 1e-5
+    ref = np.array([(exact.onsager_lnz_1d(x + e) - exact.onsager_lnz_1d(x - e)) / (2 * e) for x in b])
+    assert np.max(np.abs(d - ref)) < 1e-4
+
+
+@pytest.mark.gpu
+def test_ising_grid_against_stored_oracle():
+    path = os.path.join(os.path.dirname(__file__), "golden", "c2_grid.json")
+    if not os.path.exists(path):
+        pytest.skip("golden c2_grid not generated")
+    g = json.load(open(path))
+    pts = g["points"]
+    idx = list(range(0, 64, 9))          # 8 of the 64 grid points
+    from paper_1912_02780_gb300.observables import ising_thermodynamics
+    betas = np.array([pts[i]["beta"] for i in idx])
+    res = ising_thermodynamics(betas, g["d_cut"], g["n_steps"], "bf16x6", split_from_step=7)
+    lnz_ref = np.array([pts[i]["lnz"] for i in idx])
+    u_ref = -np.array([pts[i]["dlnz_dbeta"] for i in idx])
+    df = np.abs(res["lnz"] - lnz_ref) / betas
+    du = np.abs(res["u"] - u_ref) / np.abs(u_ref)
+    print(f"c2 grid: max |df| = {df.max():.2e}, max rel du = {du.max():.2e}")
+    assert df.max() < 1e-9
+    assert du.max() < 1e-6
