@@ -25,7 +25,9 @@ def test_grid_derivative_matches_onsager_energy_derivative():
     d = grid_derivative(b, lnz)
     e = 1e-5
     ref = np.array([(exact.onsager_lnz_1d(x + e) - exact.onsager_lnz_1d(x - e)) / (2 * e) for x in b])
-    assert np.max(np.abs(d - ref)) < 1e-4
+    err = np.abs(d - ref)
+    assert np.max(err[1:-1]) < 5e-5          # central differences, O(h^2)
+    assert max(err[0], err[-1]) < 1e-3       # one-sided at the ends, larger O(h^2) constant
 
 
 @pytest.mark.gpu
