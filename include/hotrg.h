@@ -171,7 +171,8 @@ hotrg_status hotrg_device_supports_split(void);
  * its hotrg_plan_workspace_bytes against hbm_budget_bytes; slots keep built
  * plans for reuse by later requests of the same shape and free idle ones when
  * a new plan would not fit.  A request whose plan alone exceeds the budget
- * finishes with status HOTRG_ENOMEM.  Times are seconds since the server was
+ * finishes with status HOTRG_ENOMEM.  Requests without gradients use the
+ * randomized subspace eigensolver (eigh_mode 1, 2 power iterations).  Times are seconds since the server was
  * created.  Submit, poll, wait, drain and stats are thread-safe. */
 typedef struct hotrg_server_s* hotrg_server;
 typedef struct {

@@ -131,6 +131,10 @@ void worker(hotrg_server_s* s, int slot) {
     cfg.precision = r.precision;
     cfg.split_from_step = r.split_from_step > 0 ? r.split_from_step : 1;
     cfg.want_grad = r.want_grad ? 1 : 0;
+    // forward-only requests take the randomized subspace eigensolver (the
+    // backward's eigensolve adjoint needs all eigenpairs)
+    cfg.eigh_mode = r.want_grad ? 0 : 1;
+    cfg.eigh_power_iters = 2;
     size_t bytes = 0;
     hotrg_status st = hotrg_plan_workspace_bytes(&cfg, &bytes);
     hotrg_plan plan = nullptr;
