@@ -224,6 +224,18 @@ hotrg_status hotrg_profile_read(hotrg_plan plan, double* ms, int* counts);
 /* Number of kernels this library has launched in this process (all plans). */
 unsigned long long hotrg_kernel_launches(void);
 
+/* Failure-detection hooks (tests of the error paths without a GPU fault).
+ * hotrg_debug_inject(what, arg), process-wide until reset with what = 0:
+ *   1 = the arg-th device allocation after this call fails (-> HOTRG_ENOMEM),
+ *   2 = the eigensolver of step arg reports failure (-> HOTRG_ENOTCONV),
+ *   3 = a NaN is written into the new tensor of step arg (-> HOTRG_ENONFINITE).
+ * hotrg_check_bounded_wait(timeout_ms) runs a one-thread kernel that waits on an
+ * mbarrier nothing arrives at, with the given limit instead of the library's
+ * 2 s; it returns HOTRG_ETIMEOUT when the bounded wait gave up and reported it
+ * (the expected outcome), leaving the device usable. */
+hotrg_status hotrg_debug_inject(int what, int arg);
+hotrg_status hotrg_check_bounded_wait(double timeout_ms);
+
 /* Kernel checks (used by the test-suite; not part of the HOTRG path).
  * C = A B^T for row-major float64 host matrices A (M x K), B (N x K), C (M x N),
  * computed on the device by the split-BF16 tensor-core GEMM (planes = 2 or 3

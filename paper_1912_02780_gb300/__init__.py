@@ -36,6 +36,7 @@ EXPORTS = (
     "hotrg_gemm_split_noalloc",
     "hotrg_server_create", "hotrg_server_submit", "hotrg_server_poll", "hotrg_server_wait",
     "hotrg_server_drain", "hotrg_server_get_stats", "hotrg_server_destroy",
+    "hotrg_debug_inject", "hotrg_check_bounded_wait",
 )
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
@@ -126,6 +127,8 @@ def lib() -> ctypes.CDLL:
     L.hotrg_server_drain.argtypes = [vp]
     L.hotrg_server_get_stats.argtypes = [vp, ctypes.POINTER(hotrg_server_stats)]
     L.hotrg_server_destroy.argtypes = [vp]
+    L.hotrg_debug_inject.argtypes = [ctypes.c_int, ctypes.c_int]
+    L.hotrg_check_bounded_wait.argtypes = [ctypes.c_double]
     L.hotrg_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",

@@ -68,12 +68,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
 
 // Bounded wait: true when the phase with this parity completed, false (and
 // the error word set) after about two seconds.
-__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err) {
+__device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
+                                       long long limit = kTimeoutCycles) {
   if (mbar_try_wait(bar, parity)) return true;
   long long t0 = clock64();
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (clock64() - t0 > kTimeoutCycles) {
+    if (clock64() - t0 > limit) {
       atomicOr(err, kErrTimeout);
       return false;
     }
@@ -575,7 +576,24 @@ cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cuda
   return cudaGetLastError();
 }
 
+// Self-test of the bounded wait: one thread waits on an mbarrier that nothing
+// arrives at; the wait must give up after `limit` cycles and set kErrTimeout.
+__global__ void bounded_wait_probe_kernel(int* err, long long limit) {
+  __shared__ __align__(8) uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(smem_u32(&bar), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    mbar_wait(smem_u32(&bar), 0, err, limit);
+  }
+}
+
 }  // namespace
+
+cudaError_t bounded_wait_probe(int* err, long long limit_cycles, cudaStream_t stream) {
+  count_launch();
+  bounded_wait_probe_kernel<<<1, 32, 0, stream>>>(err, limit_cycles);
+  return cudaGetLastError();
+}
 
 void tc_set_pairs(TcGemm& g, int nplanes) {
   // Product 0 must be hi * hi: it is accumulated exactly in its own TMEM buffer.

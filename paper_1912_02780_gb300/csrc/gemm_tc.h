@@ -39,6 +39,10 @@ struct TcGemm {
 // i + j <= nplanes - 1 (3, 6 or 10 products for 2, 3 or 4 planes), hi * hi first.
 void tc_set_pairs(TcGemm& g, int nplanes);
 
+// Launch a single-thread kernel whose mbarrier wait can never complete; it
+// gives up after limit_cycles and sets kErrTimeout in *err (self-test).
+cudaError_t bounded_wait_probe(int* err, long long limit_cycles, cudaStream_t stream);
+
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,
                     int num_sms);
 

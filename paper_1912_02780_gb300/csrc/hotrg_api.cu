@@ -173,6 +173,12 @@ namespace {
 
 std::atomic<unsigned long long> g_launches{0};
 
+// Host-side fault injection (tests of the error paths without a GPU fault):
+// what = 1: the arg-th device allocation fails; 2: the eigensolver of step arg
+// reports failure; 3: a NaN is written into the tensor of step arg.
+std::atomic<int> g_inj_what{0}, g_inj_arg{0}, g_inj_count{0};
+enum { kInjAlloc = 1, kInjEigh = 2, kInjNaN = 3 };
+
 // Brackets one stage of the path with CUDA events on the plan's stream when
 // profiling is on (slot = stage id, + 16 for the FP64 variant of a contraction).
 struct Stage {
@@ -211,6 +217,8 @@ hotrg_status dalloc(hotrg_plan p, T** ptr, long long elems) {
   *ptr = nullptr;
   if (elems <= 0) return HOTRG_OK;
   void* v = nullptr;
+  if (g_inj_what.load() == kInjAlloc && g_inj_count.fetch_add(1) + 1 == g_inj_arg.load())
+    return fail(p, HOTRG_ENOMEM, "cudaMalloc failed (injected)");
   if (cudaMalloc(&v, (size_t)elems * sizeof(T)) != cudaSuccess) {
     cudaGetLastError();
     return fail(p, HOTRG_ENOMEM, "cudaMalloc failed");
@@ -547,6 +555,8 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     ncols = s.Xp + 1;
   }
   CK(eigh_info_check(p->info, p->err, st));
+  if (g_inj_what.load() == kInjEigh && g_inj_arg.load() == k)
+    CK(set_value(nullptr, 0.0, p->err, kErrEigh, st));
   CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
   CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
   }
@@ -554,6 +564,8 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   else r = contract_f64(p, s, T, Ek, Tout);
   if (r != HOTRG_OK) return r;
   const long long n_out = (long long)s.Y * s.Y * s.Xp * s.Xp;
+  if (g_inj_what.load() == kInjNaN && g_inj_arg.load() == k)
+    CK(set_value(Tout, std::nan(""), nullptr, 0, st));
   Stage sc(p, kStNorm);
   CK(frob_normalize(Tout, n_out, p->partial, kMaxPartial, p->log_norms + (k - 1), p->scal, p->err,
                     st, p->sms));
@@ -757,6 +769,35 @@ void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 extern "C" {
 
 unsigned long long hotrg_kernel_launches(void) { return g_launches.load(); }
+
+hotrg_status hotrg_debug_inject(int what, int arg) {
+  if (what < 0 || what > 3) return HOTRG_EINVAL;
+  g_inj_count.store(0);
+  g_inj_arg.store(arg);
+  g_inj_what.store(what);
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_check_bounded_wait(double timeout_ms) {
+  if (!(timeout_ms > 0.0) || timeout_ms > 10000.0) return HOTRG_EINVAL;
+  int dev = 0, khz = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0)
+    return HOTRG_ECUDA;
+  int* err = nullptr;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return HOTRG_ENOMEM;
+  hotrg_status st = HOTRG_OK;
+  int e = 0;
+  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+      bounded_wait_probe(err, (long long)(timeout_ms * khz), 0) != cudaSuccess ||
+      cudaDeviceSynchronize() != cudaSuccess ||
+      cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
+    st = HOTRG_ECUDA;
+  else if (e & kErrTimeout)
+    st = HOTRG_ETIMEOUT;
+  cudaFree(err);
+  return st;
+}
 
 hotrg_status hotrg_profile_enable(hotrg_plan p, int enable) {
   if (!p) return HOTRG_EINVAL;

@@ -395,6 +395,13 @@ __global__ void fill_random_kernel(double* __restrict__ x, long long n, unsigned
   }
 }
 
+__global__ void set_value_kernel(double* x, double v, int* err, int bits) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    if (x) *x = v;
+    if (err && bits) atomicOr(err, bits);
+  }
+}
+
 __global__ void dot16_kernel(const double* __restrict__ a, const double* __restrict__ b, int n,
                              double* out) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
@@ -545,6 +552,12 @@ cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream
 cudaError_t fill_random(double* x, long long n, unsigned long long seed, cudaStream_t st, int sms) {
   count_launch();
   fill_random_kernel<<<blocks_for(n, sms), 256, 0, st>>>(x, n, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t set_value(double* x, double v, int* err, int bits, cudaStream_t st) {
+  count_launch();
+  set_value_kernel<<<1, 32, 0, st>>>(x, v, err, bits);
   return cudaGetLastError();
 }
 

@@ -39,6 +39,8 @@ cudaError_t scale_copy(const double* x, double* y, long long n, double a, cudaSt
 // x <- x * exp(-*logc)  (divide by a norm whose log lives on the device)
 cudaError_t scale_exp_neg(double* x, long long n, const double* logc, cudaStream_t st, int sms);
 cudaError_t fill_random(double* x, long long n, unsigned long long seed, cudaStream_t st, int sms);
+// *x = v (if x) and *err |= bits (if err): used by the fault-injection hooks.
+cudaError_t set_value(double* x, double v, int* err, int bits, cudaStream_t st);
 cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st);
 
 }  // namespace hotrg
