@@ -41,6 +41,14 @@ enum : int {
   kErrBounds = 8        // an index check failed (access skipped)
 };
 
+// Report a device-side failure: err[0] accumulates every bit seen, err[1]
+// keeps the first one (the root cause when one failure leads to others).
+// Every error word handed to a kernel is an array of two ints.
+__device__ __forceinline__ void report_error(int* err, int bit) {
+  atomicOr(err, bit);
+  atomicCAS(err + 1, 0, bit);
+}
+
 // Split a float into bf16 planes: v ~= p0 + p1 (+ p2), each plane the
 // round-to-nearest bf16 of the remainder left by the planes before it.
 __device__ __forceinline__ void split_bf16(float v, int nplanes, __nv_bfloat16* out) {

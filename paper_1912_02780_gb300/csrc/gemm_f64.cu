@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmF64 p, int k_per_spli
       double av = 0.0;
       if (ro >= 0 && co >= 0) {
         if (ro + co < p.a_lim) av = p.A[ro + co];
-        else atomicOr(p.err, kErrBounds);
+        else report_error(p.err, kErrBounds);
       }
       As[kk][rr] = av;
       if (p.b_kfast) { kk = idx % BK; rr = idx / BK; } else { rr = idx % BN; kk = idx / BN; }
@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmF64 p, int k_per_spli
       double bv = 0.0;
       if (ro >= 0 && co >= 0) {
         if (ro + co < p.b_lim) bv = p.B[ro + co];
-        else atomicOr(p.err, kErrBounds);
+        else report_error(p.err, kErrBounds);
       }
       Bs[kk][rr] = bv;
     }
@@ -92,7 +92,7 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmF64 p, int k_per_spli
       if (n >= p.N) continue;
       const long long off = cr + imap(p.cn, n);
       if (off < 0 || off >= p.c_lim) {
-        atomicOr(p.err, kErrBounds);
+        report_error(p.err, kErrBounds);
         continue;
       }
       double* c = p.C + off;
@@ -118,7 +118,7 @@ __global__ void splitk_reduce_kernel(GemmF64 p, int splits) {
     for (int z = 0; z < splits; ++z) s += p.ws[(long long)z * total + i];
     const long long off = imap(p.cm, m) + imap(p.cn, n);
     if (off < 0 || off >= p.c_lim) {
-      atomicOr(p.err, kErrBounds);
+      report_error(p.err, kErrBounds);
       continue;
     }
     double* c = p.C + off;
@@ -134,7 +134,7 @@ __global__ void scale_out_kernel(GemmF64 p) {
     int m = (int)(i / p.N), n = (int)(i % p.N);
     const long long off = imap(p.cm, m) + imap(p.cn, n);
     if (off < 0 || off >= p.c_lim) {
-      atomicOr(p.err, kErrBounds);
+      report_error(p.err, kErrBounds);
       continue;
     }
     double* c = p.C + off;

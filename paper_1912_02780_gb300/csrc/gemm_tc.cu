@@ -75,7 +75,7 @@ __device__ __noinline__ bool mbar_wait(uint32_t bar, uint32_t parity, int* err,
   while (true) {
     if (mbar_try_wait(bar, parity)) return true;
     if (clock64() - t0 > limit) {
-      atomicOr(err, kErrTimeout);
+      report_error(err, kErrTimeout);
       return false;
     }
   }
@@ -275,7 +275,7 @@ __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff
     if (co < 0) continue;
     long long off = coff + co;
     if (off >= p.c_lim) {
-      atomicOr(p.err, kErrBounds);
+      report_error(p.err, kErrBounds);
       continue;
     }
     if (p.out_mode == kOutF32) {

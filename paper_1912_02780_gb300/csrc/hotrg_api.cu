@@ -745,8 +745,10 @@ hotrg_status run_backward(hotrg_plan p) {
 }
 
 hotrg_status check_device_error(hotrg_plan p) {
-  int e = 0;
-  CK(cudaMemcpy(&e, p->err, sizeof(int), cudaMemcpyDeviceToHost));
+  int w[2] = {0, 0};
+  CK(cudaMemcpy(w, p->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  // the first failure recorded is the root cause; report it first
+  const int e = w[1] ? w[1] : w[0];
   if (e & kErrTimeout) return fail(p, HOTRG_ETIMEOUT, "device wait timed out");
   if (e & kErrEigh) return fail(p, HOTRG_ENOTCONV, "eigensolver did not converge");
   if (e & kErrNonFinite) return fail(p, HOTRG_ENONFINITE, "norm or trace not finite");
@@ -785,10 +787,10 @@ hotrg_status hotrg_check_bounded_wait(double timeout_ms) {
       cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess || khz <= 0)
     return HOTRG_ECUDA;
   int* err = nullptr;
-  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) return HOTRG_ENOMEM;
+  if (cudaMalloc(&err, 2 * sizeof(int)) != cudaSuccess) return HOTRG_ENOMEM;
   hotrg_status st = HOTRG_OK;
   int e = 0;
-  if (cudaMemset(err, 0, sizeof(int)) != cudaSuccess ||
+  if (cudaMemset(err, 0, 2 * sizeof(int)) != cudaSuccess ||
       bounded_wait_probe(err, (long long)(timeout_ms * khz), 0) != cudaSuccess ||
       cudaDeviceSynchronize() != cudaSuccess ||
       cudaMemcpy(&e, err, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess)
@@ -1023,7 +1025,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       ALC(p->swork, (long long)ls);
     }
   }
-  if (cudaMemset(p->err, 0, sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
+  if (cudaMemset(p->err, 0, 2 * sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
 #undef ALC
   *out = p;
   return HOTRG_OK;
@@ -1044,7 +1046,7 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
   if (!p || !T0_dev) return fail(p, HOTRG_EINVAL, "null argument");
   const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
   p->have_fwd = false;
-  CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), p->stream));
   if (T0_dev != p->T[0])
     CK(cudaMemcpyAsync(p->T[0], T0_dev, sizeof(double) * n0, cudaMemcpyDeviceToDevice, p->stream));
   hotrg_status r = run_forward(p);
@@ -1102,7 +1104,7 @@ hotrg_status hotrg_backward_device(hotrg_plan p, double* grad_dev) {
   if (!p) return HOTRG_EINVAL;
   if (!p->cfg.want_grad) return fail(p, HOTRG_ESTATE, "plan created with want_grad = 0");
   if (!p->have_fwd) return fail(p, HOTRG_ESTATE, "backward needs a forward first");
-  CK(cudaMemsetAsync(p->err, 0, sizeof(int), p->stream));
+  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), p->stream));
   hotrg_status r = run_backward(p);
   if (r != HOTRG_OK) return r;
   if (grad_dev) {
@@ -1204,13 +1206,14 @@ hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk,
       cudaMalloc(&dB, sizeof(double) * N * (size_t)K) != cudaSuccess ||
       cudaMalloc(&dC, sizeof(double) * M * (size_t)N) != cudaSuccess ||
       cudaMalloc(&pa, 2 * sa * planes) != cudaSuccess ||
-      cudaMalloc(&pb, 2 * sb * planes) != cudaSuccess || cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&pb, 2 * sb * planes) != cudaSuccess ||
+      cudaMalloc(&err, 2 * sizeof(int)) != cudaSuccess) {
     status = HOTRG_ENOMEM;
     goto done;
   }
   cudaMemcpy(dA, A, sizeof(double) * M * (size_t)K, cudaMemcpyHostToDevice);
   cudaMemcpy(dB, B, sizeof(double) * N * (size_t)K, cudaMemcpyHostToDevice);
-  cudaMemset(err, 0, sizeof(int));
+  cudaMemset(err, 0, 2 * sizeof(int));
   grid_split(dA, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, 0, sms);
   grid_split(dB, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, 0, sms);
   tc_set_pairs(g, planes);
@@ -1246,12 +1249,12 @@ hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const do
   if (cudaMalloc(&dA, sizeof(double) * M * (size_t)K) != cudaSuccess ||
       cudaMalloc(&dB, sizeof(double) * N * (size_t)K) != cudaSuccess ||
       cudaMalloc(&dC, sizeof(double) * M * (size_t)N) != cudaSuccess ||
-      cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+      cudaMalloc(&err, 2 * sizeof(int)) != cudaSuccess) {
     status = HOTRG_ENOMEM;
   } else {
     cudaMemcpy(dA, A, sizeof(double) * M * (size_t)K, cudaMemcpyHostToDevice);
     cudaMemcpy(dB, B, sizeof(double) * N * (size_t)K, cudaMemcpyHostToDevice);
-    cudaMemset(err, 0, sizeof(int));
+    cudaMemset(err, 0, 2 * sizeof(int));
     GemmF64 g;
     g.A = dA; g.am = map_lin(K); g.ak = map_lin(1);
     g.B = dB; g.bn = map_lin(K); g.bk = map_lin(1);

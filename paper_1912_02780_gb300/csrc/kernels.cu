@@ -32,7 +32,7 @@ __global__ void gather_split_kernel(const double* __restrict__ src, long long sr
     const long long off = imap(rm, r) + imap(km, k);
     double v = 0.0;
     if (off >= 0 && off < src_lim) v = src[off];
-    else atomicOr(err, kErrBounds);
+    else report_error(err, kErrBounds);
     __nv_bfloat16 b[3];
     split_bf16_d(v, nplanes, b);
     dst[i] = b[0];
@@ -88,7 +88,7 @@ __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_li
           const long long off = roff + imap(km, k0 + i);
           vd[i] = 0.0;
           if (off >= 0 && off < src_lim) vd[i] = (double)src[off];
-          else atomicOr(err, kErrBounds);
+          else report_error(err, kErrBounds);
         }
       }
     } else {
@@ -204,7 +204,7 @@ __global__ void norm_finalize_kernel(const double* __restrict__ partial, int np,
     if (threadIdx.x == 0) {
       double c = sqrt(s);
       if (!(c > 0.0) || !isfinite(c)) {
-        atomicOr(err, kErrNonFinite);
+        report_error(err, kErrNonFinite);
         c = 1.0;
       }
       *log_norm = log(c);
@@ -241,7 +241,7 @@ __global__ void trace_lnz_kernel(const double* __restrict__ T, int P, int Q,
       scale *= 0.5;
       acc += log_norms[k] * scale;
     }
-    if (!(fabs(tr) > 0.0) || !isfinite(tr)) atomicOr(err, kErrNonFinite);
+    if (!(fabs(tr) > 0.0) || !isfinite(tr)) report_error(err, kErrNonFinite);
     out[0] = acc + log(fabs(tr)) * scale;
     out[1] = tr >= 0.0 ? 1.0 : -1.0;
     for (int k = 0; k < n; ++k) out[2 + k] = log_norms[k];
@@ -330,7 +330,7 @@ __global__ void eig_diag_kernel(const double* __restrict__ lam, int nlam, int N,
 }
 
 __global__ void eigh_info_kernel(const int* info, int* err) {
-  if (threadIdx.x == 0 && *info != 0) atomicOr(err, kErrEigh);
+  if (threadIdx.x == 0 && *info != 0) report_error(err, kErrEigh);
 }
 
 // Backward seed: E = delta(a,a') delta(b,b') / trace on a (P, P, Q, Q) tensor.
@@ -398,7 +398,7 @@ __global__ void fill_random_kernel(double* __restrict__ x, long long n, unsigned
 __global__ void set_value_kernel(double* x, double v, int* err, int bits) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     if (x) *x = v;
-    if (err && bits) atomicOr(err, bits);
+    if (err && bits) report_error(err, bits);
   }
 }
 

@@ -74,8 +74,9 @@ extern "C" hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes
   __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(base + kHeader);
   __nv_bfloat16* pb = pa + (size_t)planes * sa;
   const int sms = prop.multiProcessorCount;
-  // The scratch keeps the previous call's contents: the error word must start at zero.
-  if (cudaMemsetAsync(err, 0, sizeof(int), s) != cudaSuccess) return HOTRG_ECUDA;
+  // The scratch keeps the previous call's contents: the error words (all bits
+  // seen, first bit seen) must start at zero.
+  if (cudaMemsetAsync(err, 0, 2 * sizeof(int), s) != cudaSuccess) return HOTRG_ECUDA;
   if (gather_split(A_dev, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, s,
                    sms) != cudaSuccess ||
       gather_split(B_dev, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, s,
