@@ -281,6 +281,8 @@ def main():
     ap.add_argument("--eigh-mode", type=int, default=1,
                     help="0: cuSOLVER partial eigensolve; 1: randomized subspace eigensolver")
     ap.add_argument("--power-iters", type=int, default=2)
+    ap.add_argument("--eigh-block", type=int, default=0,
+                    help="vectors in the subspace eigensolver's block (0: 4 D_cut)")
     ap.add_argument("--concurrent", type=int, default=1,
                     help="independent solves (seeds) per GPU per step, run concurrently "
                          "(5 measured 0.130 vs 0.121 solves/s for 1 at D_cut = 64: the FP64 "
@@ -325,7 +327,8 @@ def main():
     plans = [hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
                       want_grad=bool(args.grad), stream=st.cuda_stream,
                       hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
-                      eigh_power_iters=args.power_iters) for st in streams]
+                      eigh_power_iters=args.power_iters, eigh_block=args.eigh_block)
+             for st in streams]
     T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
     out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]
     grad_devs = [torch.zeros(d0 ** 4, dtype=torch.float64, device=dev) for _ in range(C)]
@@ -438,7 +441,8 @@ def main():
             "config": {"workload": args.workload, "desc": desc, "d0": d0, "d_cut": d_cut,
                        "n_steps": n, "precision": args.precision,
                        "split_from_step": args.split_from, "hi_precision_steps": args.hi_steps,
-                       "eigh": ("randomized subspace, %d power iterations" % args.power_iters
+                       "eigh": ("randomized subspace, block %d, %d power iterations"
+                                % (args.eigh_block or 4 * d_cut, args.power_iters)
                                 if args.eigh_mode == 1 else "cuSOLVER syevdx (top D'+1)"),
                        "grad": bool(args.grad), "solves_per_step": C,
                        "seeds": seeds,

@@ -88,20 +88,28 @@ typedef struct {
                                four bf16 planes (10 products, ~32 significant bits) instead of
                                three; these steps weigh most in ln Z / N (weight 2^-k)     */
   int eigh_mode;            /* plans without gradients: 0 = cuSOLVER partial eigensolve of the
-                               D'+1 largest pairs; 1 = randomized subspace eigensolver (FP64
-                               block power iteration on 4 D' vectors with Householder QR,
-                               then Rayleigh-Ritz; used where 4 D' < X^2).  Plans with
-                               gradients always take all eigenpairs.                      */
+                               D'+1 largest pairs; 1 = randomized subspace eigensolver (block
+                               power iteration on eigh_block vectors with FP64 Householder QR,
+                               then FP64 Rayleigh-Ritz; the products G Q run on the
+                               four-plane tensor-core GEMM on split steps, in FP64
+                               otherwise; used where 4 D' < X^2).  Plans with gradients
+                               always take all eigenpairs.                                */
   int eigh_power_iters;     /* power iterations of eigh_mode 1 (<= 0: 4)                   */
+  int eigh_block;           /* vectors in the block of eigh_mode 1 (<= 0: 4 D'; at least
+                               D' + 1)                                                     */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
 
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
- * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4.
+ * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
+
+/* sizeof(hotrg_config) as compiled into the library, so that a binding can
+ * check that its copy of the struct matches. */
+size_t hotrg_config_sizeof(void);
 
 /* Device bytes a plan with this config would allocate (for admission control). */
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* cfg, size_t* bytes);
@@ -215,8 +223,9 @@ void hotrg_server_destroy(hotrg_server server);
  * 3 stage-2 contraction (the O(D^7) GEMM), 4 stage-3 contraction, 5 norm,
  * 6 operand preparation (bf16 split), 7 backward contractions, 8 backward
  * eigensolve adjoint, 9 backward Gram adjoint, 10 stage-2 contraction of the
- * four-plane steps; slot + 16 = the same stage run by the FP64 GEMM instead of
- * the tensor-core GEMM. */
+ * four-plane steps; inside slot 1, for the subspace eigensolver: 11 products
+ * G Q (with the split of G), 12 QR, 13 Rayleigh-Ritz; slot + 16 = the same
+ * stage run by the FP64 GEMM instead of the tensor-core GEMM. */
 #define HOTRG_PROFILE_SLOTS 32
 hotrg_status hotrg_profile_enable(hotrg_plan plan, int enable);
 hotrg_status hotrg_profile_read(hotrg_plan plan, double* ms, int* counts);

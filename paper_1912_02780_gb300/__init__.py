@@ -27,7 +27,7 @@ STATUS = {0: "HOTRG_OK", 1: "HOTRG_EINVAL", 2: "HOTRG_ENOMEM", 3: "HOTRG_ECUDA",
 
 # Every symbol declared in include/hotrg.h.
 EXPORTS = (
-    "hotrg_config_default", "hotrg_plan_workspace_bytes", "hotrg_plan_create",
+    "hotrg_config_default", "hotrg_config_sizeof", "hotrg_plan_workspace_bytes", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
     "hotrg_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
@@ -40,7 +40,8 @@ EXPORTS = (
 )
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
-               7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj", 10: "s2_4plane"}
+               7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj", 10: "s2_4plane",
+               11: "eigh_prod", 12: "eigh_qr", 13: "eigh_rr"}
 
 
 class hotrg_config(ctypes.Structure):
@@ -49,7 +50,7 @@ class hotrg_config(ctypes.Structure):
                 ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
                 ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
                 ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
-                ("eigh_power_iters", ctypes.c_int)]
+                ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -132,8 +133,14 @@ def lib() -> ctypes.CDLL:
     L.hotrg_server_destroy.restype = None
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
-                        "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy"):
+                        "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy",
+                        "hotrg_config_sizeof"):
             getattr(L, name).restype = ctypes.c_int
+    L.hotrg_config_sizeof.argtypes = []
+    L.hotrg_config_sizeof.restype = ctypes.c_size_t
+    if L.hotrg_config_sizeof() != ctypes.sizeof(hotrg_config):
+        raise RuntimeError(f"hotrg_config layout mismatch: library {L.hotrg_config_sizeof()} bytes, "
+                           f"binding {ctypes.sizeof(hotrg_config)} bytes (rebuild the library)")
     _LIB = L
     return L
 
@@ -146,7 +153,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 want_grad: bool = True, fixed_w_grad: bool = False,
                 eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
                 hi_precision_steps: int = 2, eigh_mode: int = 0,
-                eigh_power_iters: int = 4) -> hotrg_config:
+                eigh_power_iters: int = 4, eigh_block: int = 0) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -158,6 +165,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.hi_precision_steps = hi_precision_steps
     c.eigh_mode = eigh_mode
     c.eigh_power_iters = eigh_power_iters
+    c.eigh_block = eigh_block
     return c
 
 
@@ -182,10 +190,10 @@ class Plan:
                  split_from_step: int = 1, want_grad: bool = True, fixed_w_grad: bool = False,
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
                  gram_split_from_step: int = 0, hi_precision_steps: int = 2,
-                 eigh_mode: int = 0, eigh_power_iters: int = 4):
+                 eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
-                               hi_precision_steps, eigh_mode, eigh_power_iters)
+                               hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

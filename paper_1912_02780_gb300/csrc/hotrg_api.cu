@@ -327,7 +327,7 @@ TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long 
 
 enum StageId { kStGram = 0, kStEigh = 1, kStS1 = 2, kStS2 = 3, kStS3 = 4, kStNorm = 5,
                kStPrep = 6, kStBwdContract = 7, kStBwdEigh = 8, kStBwdGram = 9, kStS2Hi = 10,
-               kStF64 = 16 };
+               kStEighProd = 11, kStEighQR = 12, kStEighRR = 13, kStF64 = 16 };
 
 hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* A, double* B,
                       double* G) {
@@ -462,33 +462,72 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
 
 double* E_of(hotrg_plan p, int k) { return p->cfg.want_grad ? p->E[k - 1] : p->E[0]; }
 
-bool use_subspace(const hotrg_plan p, const StepGeom& s) {
-  return p->cfg.eigh_mode == 1 && !p->cfg.want_grad && 4LL * s.Xp < s.N;
+// Block size of the subspace eigensolver at a step (D' + 1 at least: the
+// kept vectors and one more for the gap).
+int subspace_k(const hotrg_config& c, const StepGeom& s) {
+  const int k = c.eigh_block > 0 ? c.eigh_block : 4 * s.Xp;
+  return k > s.Xp + 1 ? k : s.Xp + 1;
 }
 
+bool subspace_applies(const hotrg_config& c, const StepGeom& s) {
+  return c.eigh_mode == 1 && !c.want_grad && (long long)subspace_k(c, s) < s.N;
+}
+
+bool use_subspace(const hotrg_plan p, const StepGeom& s) { return subspace_applies(p->cfg, s); }
+
 // Randomized subspace eigensolver for the leading eigenpairs of the symmetric
-// PSD Gram matrix G (N x N, in p->Escr): a block of k = 4 D' vectors, started
-// from a deterministic pseudo-random block, is multiplied by G eigh_power_iters
-// times with a Householder QR (cuSOLVER geqrf + orgqr) after each product, and
-// the Rayleigh-Ritz problem Q^T G Q (k x k, cuSOLVER syevd) gives the Ritz
-// pairs.  All in FP64.  The block is stored as k contiguous vectors of length
-// N, i.e. an N x k column-major matrix for cuSOLVER.  Output: the k Ritz
-// vectors (ascending Ritz values) in p->Zs as contiguous rows and the Ritz
+// PSD Gram matrix G (N x N, in p->Escr): a block of k vectors (eigh_block,
+// default 4 D'), started
+// from a deterministic pseudo-random block, is multiplied by G
+// eigh_power_iters times with a Householder QR (cuSOLVER geqrf + orgqr) after
+// each product, and the Rayleigh-Ritz problem Q^T G Q (k x k, cuSOLVER syevd)
+// gives the Ritz pairs.  The random start is not orthonormalised: only the span
+// of the block matters to the iteration.  On split steps the products G Q run
+// on the tensor cores with four-plane operands (10 products, G split once per
+// step, FP64 output); the QR, the projection Q^T (G Q), the small eigensolve and
+// the Ritz vectors stay in FP64.  The block is stored as k contiguous vectors
+// of length N, i.e. an N x k column-major matrix for cuSOLVER.  Output: the k
+// Ritz vectors (ascending Ritz values) in p->Zs as contiguous rows and the Ritz
 // values in p->wasc, ready for eig_desc.
+constexpr int kEighPlanes = 4;
+
+bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
+  if (!s.split || !p->pU || !p->pV) return false;
+  const long long N = s.N, K = subspace_k(p->cfg, s);
+  const long long cap = p->L.chunkS * p->L.np_max;
+  return N % 8 == 0 && kEighPlanes * round_up(N * N, 64) <= cap &&
+         kEighPlanes * round_up(K * N, 64) <= cap;
+}
+
 hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
   cudaStream_t st = p->stream;
-  const int N = (int)s.N, K = 4 * s.Xp;
+  const int N = (int)s.N, K = subspace_k(p->cfg, s);
   const int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
-  CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
-  for (int it = 0; it <= iters; ++it) {
-    if (it > 0) {
-      // Z = G Q (as rows: Z[a][i] = sum_j Q[a][j] G[i][j]), then Q = orth(Z)
+  const bool tc = subspace_on_tc(p, s);
+  const long long sG = round_up((long long)N * N, 64), sQ = round_up((long long)K * N, 64);
+  if (tc) {
+    Stage sc(p, kStEighProd);
+    CK(gsplit(p, p->Escr, map_lin(N), map_lin(1), N, N, kEighPlanes, sG, p->pV));
+  }
+  // Zs = G Qs, as rows: Z[a][i] = sum_j Q[a][j] G[i][j]
+  auto product = [&]() -> hotrg_status {
+    Stage sc(p, kStEighProd);
+    if (tc) {
+      CK(gsplit(p, p->Qs, map_lin(N), map_lin(1), K, N, kEighPlanes, sQ, p->pU));
+      CK(tc_gemm(opnd(p->pU, K, N, kEighPlanes, sQ), opnd(p->pV, N, N, kEighPlanes, sG),
+                 tcg(p, kEighPlanes, K, N, N, map_lin(N), map_lin(1), kOutF64, p->Zs, 0), st,
+                 p->sms));
+    } else {
       CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Escr, map_lin(N), map_lin(1), p->Zs,
                       map_lin(N), map_lin(1), K, N, N, 1.0, 0.0),
                   st, p->sms));
-      CK(cudaMemcpyAsync(p->Qs, p->Zs, sizeof(double) * (size_t)K * N, cudaMemcpyDeviceToDevice,
-                         st));
     }
+    return HOTRG_OK;
+  };
+  // Qs = orth(Zs): Householder QR (cuSOLVER geqrf + orgqr)
+  auto householder = [&]() -> hotrg_status {
+    CK(cudaMemcpyAsync(p->Qs, p->Zs, sizeof(double) * (size_t)K * N, cudaMemcpyDeviceToDevice,
+                       st));
     if (cusolverDnDgeqrf(p->solver, N, K, p->Qs, N, p->tau, p->swork, p->lswork, p->info) !=
         CUSOLVER_STATUS_SUCCESS)
       return fail(p, HOTRG_ECUDA, "cusolverDnDgeqrf failed");
@@ -497,11 +536,21 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
         CUSOLVER_STATUS_SUCCESS)
       return fail(p, HOTRG_ECUDA, "cusolverDnDorgqr failed");
     CK(eigh_info_check(p->info, p->err, st));
+    return HOTRG_OK;
+  };
+  auto orth = [&]() -> hotrg_status {
+    Stage sc(p, kStEighQR);
+    return householder();
+  };
+  CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
+  hotrg_status r;
+  for (int it = 0; it < iters; ++it) {
+    if ((r = product()) != HOTRG_OK) return r;
+    if ((r = orth()) != HOTRG_OK) return r;
   }
   // Rayleigh-Ritz: Z = G Q, H[a][b] = sum_i Q[a][i] Z[b][i]
-  CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Escr, map_lin(N), map_lin(1), p->Zs,
-                  map_lin(N), map_lin(1), K, N, N, 1.0, 0.0),
-              st, p->sms));
+  if ((r = product()) != HOTRG_OK) return r;
+  Stage sc(p, kStEighRR);
   CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Zs, map_lin(N), map_lin(1), p->Hs,
                   map_lin(K), map_lin(1), K, K, N, 1.0, 0.0),
               st, p->sms));
@@ -536,7 +585,7 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   if (use_subspace(p, s)) {
     hotrg_status rr = eigh_subspace(p, s, k);
     if (rr != HOTRG_OK) return rr;
-    ncols = 4 * s.Xp;
+    ncols = subspace_k(p->cfg, s);
     evec = p->Zs;
   } else if (p->cfg.want_grad || s.Xp >= N) {
     // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
@@ -836,6 +885,10 @@ hotrg_status hotrg_profile_read(hotrg_plan p, double* ms, int* counts) {
   return HOTRG_OK;
 }
 
+size_t hotrg_config_sizeof(void) { return sizeof(hotrg_config); }
+
+
+
 void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   if (!c) return;
   memset(c, 0, sizeof(*c));
@@ -851,6 +904,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->hi_precision_steps = 2;
   c->eigh_mode = 0;
   c->eigh_power_iters = 4;
+  c->eigh_block = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -880,6 +934,15 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
     b.add(L.chunkS > L.splitG ? L.chunkS : L.splitG, 4);
   }
   b.add(kSplitK, 8);
+  {
+    long long kmax = 0;   // subspace eigensolver blocks (two K x N, one K x K)
+    for (const StepGeom& g : L.g)
+      if (subspace_applies(*c, g) && subspace_k(*c, g) > kmax) kmax = subspace_k(*c, g);
+    if (kmax > 0) {
+      b.add(kmax * L.maxN, 8 * 2);
+      b.add(kmax * kmax, 8);
+    }
+  }
   b.total += (size_t)64 << 20;  // solver workspace and small buffers (estimate)
   *bytes = b.total;
   return HOTRG_OK;
@@ -1001,7 +1064,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     int kmax = 0;
     long long nmax = 0;
     for (const StepGeom& g : L.g)
-      if (4LL * g.Xp < g.N && 4 * g.Xp > kmax) kmax = 4 * g.Xp;
+      if (subspace_applies(*cfg, g) && subspace_k(*cfg, g) > kmax) kmax = subspace_k(*cfg, g);
     nmax = L.maxN;
     if (kmax > 0) {
       p->kspace = kmax;
@@ -1011,8 +1074,8 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       ALC(p->tau, kmax);
       int l1 = 0, l2 = 0, l3 = 0, ls = 0;
       for (const StepGeom& g : L.g) {
-        if (!(4LL * g.Xp < g.N)) continue;
-        const int Kq = 4 * g.Xp, Nq = (int)g.N;
+        if (!subspace_applies(*cfg, g)) continue;
+        const int Kq = subspace_k(*cfg, g), Nq = (int)g.N;
         if (cusolverDnDgeqrf_bufferSize(p->solver, Nq, Kq, p->Qs, Nq, &l1) != CUSOLVER_STATUS_SUCCESS ||
             cusolverDnDorgqr_bufferSize(p->solver, Nq, Kq, Kq, p->Qs, Nq, p->tau, &l2) !=
                 CUSOLVER_STATUS_SUCCESS ||

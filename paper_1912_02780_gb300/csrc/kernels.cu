@@ -42,17 +42,48 @@ __global__ void gather_split_kernel(const double* __restrict__ src, long long sr
 }
 
 // Grid-aligned split for the tensor-core GEMM.  One warp per (row, K segment
-// of `seg` <= 128 elements).  With three planes, plane 0 is the value rounded
-// to the grid g = 2^(e-8), 2^(e-1) <= max|segment| < 2^e, so |plane0 / g| <= 256
-// is an integer that bf16 holds exactly; planes 1 and 2 are the bf16
-// round-to-nearest of the remainders.  With every operand split this way, the
-// products of the two plane-0 values of a segment are integers on the grid
-// g_a g_b below 2^16, and their sum over a segment of 128 stays below 2^23:
-// the FP32 tensor-core accumulation of those products is exact.  With two
-// planes, plane 0 is the plain round-to-nearest bf16 of the value (a grid
-// would cost the remainder plane bits on small elements).
+// of `seg` <= 128 elements), kSplitSegs segments per warp iteration with all
+// their loads issued before any is used (memory-level parallelism: the kernel
+// streams the D^5 intermediates and is bound by HBM).  With three or four
+// planes, plane 0 is the value rounded to the grid g = 2^(e-8),
+// 2^(e-1) <= max|segment| < 2^e, so |plane0 / g| <= 256 is an integer that
+// bf16 holds exactly; the further planes are the bf16 round-to-nearest of the
+// remainders.  With every operand split this way, the products of the two
+// plane-0 values of a segment are integers on the grid g_a g_b below 2^16, and
+// their sum over a segment of 128 stays below 2^23: the FP32 tensor-core
+// accumulation of those products is exact.  With two planes, plane 0 is the
+// plain round-to-nearest bf16 of the value (a grid would cost the remainder
+// plane bits on small elements).
+constexpr int kSplitSegs = 4;
+
 template <typename SrcT>
-__global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm,
+__device__ __forceinline__ void split_load4(const SrcT* __restrict__ src, long long src_lim,
+                                            long long roff, const IMap& km, int k0, int contig,
+                                            SrcT* vd, int* err) {
+  const long long off0 = roff + imap(km, k0);
+  if (contig && off0 >= 0 && off0 + 3 < src_lim && (off0 & (sizeof(SrcT) == 4 ? 3 : 1)) == 0) {
+    if constexpr (sizeof(SrcT) == 4) {
+      const float4 q = __ldcs(reinterpret_cast<const float4*>(src + off0));
+      vd[0] = q.x; vd[1] = q.y; vd[2] = q.z; vd[3] = q.w;
+    } else {
+      const double2 a = *reinterpret_cast<const double2*>(src + off0);
+      const double2 b = *reinterpret_cast<const double2*>(src + off0 + 2);
+      vd[0] = a.x; vd[1] = a.y; vd[2] = b.x; vd[3] = b.y;
+    }
+    return;
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const long long off = roff + imap(km, k0 + i);
+    vd[i] = SrcT(0);
+    if (off >= 0 && off < src_lim) vd[i] = src[off];
+    else report_error(err, kErrBounds);
+  }
+}
+
+template <typename SrcT>
+__global__ void __launch_bounds__(256, sizeof(SrcT) == 4 ? 4 : 3)
+    grid_split_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm,
                                   IMap km, int rows, int K, int seg, int nplanes, int gridded,
                                   int contig, long long plane_stride,
                                   __nv_bfloat16* __restrict__ dst, int* err) {
@@ -61,84 +92,74 @@ __global__ void grid_split_kernel(const SrcT* __restrict__ src, long long src_li
   const long long nwarps = ((long long)gridDim.x * blockDim.x) >> 5;
   const int nseg = (K + seg - 1) / seg;
   const long long work = (long long)rows * nseg;
-  for (long long w = warp0; w < work; w += nwarps) {
-    const int r = (int)(w / nseg), sg = (int)(w % nseg);
-    // lane handles the 4 consecutive elements k0 .. k0 + 3 of the segment
-    const int k0 = sg * seg + 4 * lane;
-    const bool active = 4 * lane < seg && k0 < K;   // K is a multiple of 8
-    const long long roff = imap(rm, r);
-    float v[4];
-    double vd[4];
-    float mx = 0.f;
-    if (active) {
-      const long long off0 = roff + imap(km, k0);
-      if (contig && off0 >= 0 && off0 + 3 < src_lim &&
-          (off0 & (sizeof(SrcT) == 4 ? 3 : 1)) == 0) {
+  for (long long w0 = warp0 * kSplitSegs; w0 < work; w0 += nwarps * kSplitSegs) {
+    // lane handles the 4 consecutive elements k0 .. k0 + 3 of each segment
+    SrcT vd[kSplitSegs][4];   // the source precision: float sources stay float
+    long long obase[kSplitSegs];
+    bool active[kSplitSegs];
+#pragma unroll
+    for (int s = 0; s < kSplitSegs; ++s) {
+      const long long w = w0 + s;
+      const int r = (int)(w / nseg), sg = (int)(w % nseg);
+      const int k0 = sg * seg + 4 * lane;
+      active[s] = w < work && 4 * lane < seg && k0 < K;   // K is a multiple of 8
+      obase[s] = (long long)r * K + k0;                   // multiple of 4: 8-byte aligned
+      if (active[s]) {
+        split_load4(src, src_lim, imap(rm, r), km, k0, contig, vd[s], err);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vd[s][i] = SrcT(0);
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < kSplitSegs; ++s) {
+      float v[4];
+      float mx = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        v[i] = (float)vd[s][i];
+        mx = fmaxf(mx, fabsf(v[i]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+      // grid 2^(e-8) with 2^(e-1) <= max < 2^e, kept a normal float (tiny segments
+      // get a coarser grid, which keeps the plane-0 integers even smaller)
+      int e = 0;
+      frexpf(mx, &e);
+      const float g = (mx > 0.f) ? ldexpf(1.f, max(e - 8, -126)) : 1.f;
+      if (!active[s]) continue;
+      __nv_bfloat16 b[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        __nv_bfloat16 b0;
+        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
+        else b0 = __double2bfloat16((double)vd[s][i]);
+        b[0][i] = b0;
         if constexpr (sizeof(SrcT) == 4) {
-          const float4 q = *reinterpret_cast<const float4*>(src + off0);
-          vd[0] = q.x; vd[1] = q.y; vd[2] = q.z; vd[3] = q.w;
+          // float source: the remainders are exact in float
+          const float rem = v[i] - __bfloat162float(b0);
+          b[1][i] = __float2bfloat16_rn(rem);
+          const float rem2 = rem - __bfloat162float(b[1][i]);
+          b[2][i] = __float2bfloat16_rn(rem2);
+          b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
         } else {
-          const double2 a = *reinterpret_cast<const double2*>(src + off0);
-          const double2 b = *reinterpret_cast<const double2*>(src + off0 + 2);
-          vd[0] = a.x; vd[1] = a.y; vd[2] = b.x; vd[3] = b.y;
-        }
-      } else {
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-          const long long off = roff + imap(km, k0 + i);
-          vd[i] = 0.0;
-          if (off >= 0 && off < src_lim) vd[i] = (double)src[off];
-          else report_error(err, kErrBounds);
+          // double source: the first remainder as a float pair keeps the bits a
+          // float would drop (enough for four planes), the rest in float
+          const double remd = (double)vd[s][i] - (double)__bfloat162float(b0);
+          const float rh = (float)remd;
+          const float rl = (float)(remd - (double)rh);
+          b[1][i] = __float2bfloat16_rn(rh);
+          const float rem2 = (rh - __bfloat162float(b[1][i])) + rl;
+          b[2][i] = __float2bfloat16_rn(rem2);
+          b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
         }
       }
-    } else {
 #pragma unroll
-      for (int i = 0; i < 4; ++i) vd[i] = 0.0;
-    }
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      v[i] = (float)vd[i];
-      mx = fmaxf(mx, fabsf(v[i]));
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    // grid 2^(e-8) with 2^(e-1) <= max < 2^e, kept a normal float (tiny segments
-    // get a coarser grid, which keeps the plane-0 integers even smaller)
-    int e = 0;
-    frexpf(mx, &e);
-    const float g = (mx > 0.f) ? ldexpf(1.f, max(e - 8, -126)) : 1.f;
-    if (!active) continue;
-    __nv_bfloat16 b[4][4];
-#pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      __nv_bfloat16 b0;
-      if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
-      else b0 = __double2bfloat16(vd[i]);
-      b[0][i] = b0;
-      if constexpr (sizeof(SrcT) == 4) {
-        // float source: the remainders are exact in float
-        const float rem = v[i] - __bfloat162float(b0);
-        b[1][i] = __float2bfloat16_rn(rem);
-        const float rem2 = rem - __bfloat162float(b[1][i]);
-        b[2][i] = __float2bfloat16_rn(rem2);
-        b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
-      } else {
-        // double source: the first remainder as a float pair keeps the bits a
-        // float would drop (enough for four planes), the rest in float
-        const double remd = vd[i] - (double)__bfloat162float(b0);
-        const float rh = (float)remd;
-        const float rl = (float)(remd - (double)rh);
-        b[1][i] = __float2bfloat16_rn(rh);
-        const float rem2 = (rh - __bfloat162float(b[1][i])) + rl;
-        b[2][i] = __float2bfloat16_rn(rem2);
-        b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
+      for (int q = 0; q < 4; ++q) {
+        if (q >= nplanes) break;
+        *reinterpret_cast<uint2*>(dst + q * plane_stride + obase[s]) =
+            *reinterpret_cast<const uint2*>(b[q]);
       }
-    }
-    const long long o = (long long)r * K + k0;   // multiple of 4: 8-byte aligned
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q >= nplanes) break;
-      *reinterpret_cast<uint2*>(dst + q * plane_stride + o) = *reinterpret_cast<const uint2*>(b[q]);
     }
   }
 }
@@ -440,8 +461,8 @@ cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, i
   const long long work = (long long)rows * ((K + seg - 1) / seg);
   if (work == 0) return cudaSuccess;
   if ((long long)rows * K > plane_stride) return cudaErrorInvalidValue;
-  long long blocks = (work + 7) / 8;   // 8 warps per block
-  if (blocks > 32LL * sms) blocks = 32LL * sms;
+  long long blocks = (work + 8 * kSplitSegs - 1) / (8 * kSplitSegs);   // 8 warps per block
+  if (blocks > 16LL * sms) blocks = 16LL * sms;
   count_launch();
   grid_split_kernel<SrcT><<<(int)blocks, 256, 0, st>>>(src, src_lim, rm, km, rows, K, seg, nplanes,
                                                         gridded, contig, plane_stride, dst, err);
