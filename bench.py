@@ -274,8 +274,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c4_d64", choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="bf16x6", choices=["fp64", "bf16x3", "bf16x6"])
-    ap.add_argument("--split-from", type=int, default=5)
-    ap.add_argument("--hi-steps", type=int, default=2,
+    ap.add_argument("--split-from", type=int, default=4)
+    ap.add_argument("--hi-steps", type=int, default=3,
                     help="split steps (from --split-from) with four bf16 planes")
     ap.add_argument("--no-fp64-ref", action="store_true")
     ap.add_argument("--eigh-mode", type=int, default=1,

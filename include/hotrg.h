@@ -97,13 +97,18 @@ typedef struct {
   int eigh_power_iters;     /* power iterations of eigh_mode 1 (<= 0: 4)                   */
   int eigh_block;           /* vectors in the block of eigh_mode 1 (<= 0: 4 D'; at least
                                D' + 1)                                                     */
+  int epilogue_split;       /* three-plane split steps: 1 = the stage-1 and stage-2 GEMMs
+                               write their outputs as bf16 planes from the epilogue where
+                               the layout allows it; 0 = through an FP32 buffer and a
+                               separate split kernel (bit-identical results)               */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
 
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
- * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0.
+ * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
+ * epilogue_split = 1.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 

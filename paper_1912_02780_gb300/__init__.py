@@ -50,7 +50,8 @@ class hotrg_config(ctypes.Structure):
                 ("want_grad", ctypes.c_int), ("fixed_w_grad", ctypes.c_int),
                 ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
                 ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
-                ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int)]
+                ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int),
+                ("epilogue_split", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -153,7 +154,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 want_grad: bool = True, fixed_w_grad: bool = False,
                 eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
                 hi_precision_steps: int = 2, eigh_mode: int = 0,
-                eigh_power_iters: int = 4, eigh_block: int = 0) -> hotrg_config:
+                eigh_power_iters: int = 4, eigh_block: int = 0,
+                epilogue_split: bool = True) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -166,6 +168,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_mode = eigh_mode
     c.eigh_power_iters = eigh_power_iters
     c.eigh_block = eigh_block
+    c.epilogue_split = int(bool(epilogue_split))
     return c
 
 
@@ -190,10 +193,12 @@ class Plan:
                  split_from_step: int = 1, want_grad: bool = True, fixed_w_grad: bool = False,
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
                  gram_split_from_step: int = 0, hi_precision_steps: int = 2,
-                 eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0):
+                 eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0,
+                 epilogue_split: bool = True):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
-                               hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block)
+                               hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
+                               epilogue_split)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

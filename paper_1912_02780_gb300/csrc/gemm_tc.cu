@@ -125,6 +125,18 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+  uint32_t r[8];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7])
+      : "r"(taddr)
+      : "memory");
+#pragma unroll
+  for (int i = 0; i < 8; ++i) v[i] = __uint_as_float(r[i]);
+}
+
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const float* v) {
   asm volatile(
       "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
@@ -209,6 +221,18 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Tile t of an MT x NT grid: M fastest (m_fast) or N fastest.
+__device__ __forceinline__ void tile_coords(long long t, int MT, int NT, int m_fast, int& mt,
+                                            int& nt) {
+  if (m_fast) {
+    nt = (int)(t / MT);
+    mt = (int)(t - (long long)nt * MT);
+  } else {
+    mt = (int)(t / NT);
+    nt = (int)(t - (long long)mt * NT);
+  }
+}
+
 template <int BN, int NP, int BK>
 struct Cfg {
   static constexpr int kAPlane = BM * BK * 2;
@@ -219,38 +243,64 @@ struct Cfg {
   static constexpr int kThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
   static constexpr int kCols = BN / 2;                   // columns per epilogue thread
   static constexpr int kBars = 2 * kStages + 5;
-  static constexpr int kSmem = 1024 + kStages * kStage + kBars * 8 + BN * 8 + BN / 16 * 4 + 16;
+  // Shared memory after the pipeline stages (byte offsets from the 1024-aligned
+  // base): mbarriers, column offsets (BN), contiguity flags, the TMEM address,
+  // the segment-max / offset exchange of the grid-split epilogue (2 halves x
+  // 128 rows), and a 2 KB store-staging buffer per epilogue warp (16-byte
+  // aligned: it is accessed as uint4).
+  static constexpr int kStageBytes = 2048;
+  static constexpr int kOffBars = kStages * kStage;
+  static constexpr int kOffCn = kOffBars + kBars * 8;
+  static constexpr int kOffCv = kOffCn + BN * 8;
+  static constexpr int kOffTmem = kOffCv + BN / 16 * 4;
+  static constexpr int kOffXo = (kOffTmem + 16 + 15) / 16 * 16;
+  static constexpr int kOffXm = kOffXo + 2 * BM * 8;
+  static constexpr int kOffStg = (kOffXm + 2 * BM * 4 + 15) / 16 * 16;
+  static constexpr int kSmem = 1024 + kOffStg + kEpiWarps * kStageBytes;
+  static_assert(kOffCn % 8 == 0 && kOffXo % 16 == 0 && kOffStg % 16 == 0, "smem alignment");
+  static_assert(kSmem <= 232448, "shared memory per CTA");
   // TMEM: per buffer (2) an exact hi*hi accumulator and a "rest" accumulator, BN columns each.
   static constexpr int kTmemCols = 4 * BN;
   static_assert(kStages >= 2, "need at least two pipeline stages");
   static_assert(kTmemCols <= 512, "TMEM holds 512 columns");
 };
+// Warp-cooperative store of 64 bytes per lane (each lane: one contiguous,
+// 16-byte aligned destination run) through the warp's 2 KB staging buffer:
+// every store instruction then writes 8 runs x 64 bytes (whole 32-byte
+// sectors) instead of 32 runs x 16 bytes.  The 16-byte chunk position is
+// XOR-swizzled with the row so that both shared-memory passes are free of bank
+// conflicts.  All 32 lanes must take part.
+__device__ __forceinline__ void warp_store64(uint8_t* stage, const uint4 (&v)[4], char* dst,
+                                             int lane) {
+  const int sw = (lane >> 1) & 3;
+  uint4* srow = reinterpret_cast<uint4*>(stage + lane * 64);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) srow[c ^ sw] = v[c];
+  __syncwarp();
+  const int c = lane & 3;
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int r = 8 * k + (lane >> 2);
+    char* d = reinterpret_cast<char*>(
+        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), r));
+    const uint4 x = reinterpret_cast<const uint4*>(stage + r * 64)[c ^ ((r >> 1) & 3)];
+    *reinterpret_cast<uint4*>(d + c * 16) = x;
+  }
+  __syncwarp();
+}
+
+__device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  return (uint32_t)__bfloat16_as_ushort(lo) | ((uint32_t)__bfloat16_as_ushort(hi) << 16);
+}
+
 template <int BN, int NP>
 __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff,
                                                  const long long* cn_s, int contig, int cc,
                                                  const float* hi, const float* lo) {
   const long long off0 = coff + cn_s[cc];
-  if (contig && off0 >= 0 && off0 + 15 < p.c_lim && !p.accumulate) {
-    if (p.out_mode == kOutSplit && (off0 & 7) == 0) {
-      __nv_bfloat16 b[3][16];
-#pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        float h = p.alpha * hi[j], l = p.alpha * lo[j];
-        b[0][j] = __float2bfloat16_rn(h);
-        float r = (h - __bfloat162float(b[0][j])) + l;
-        b[1][j] = __float2bfloat16_rn(r);
-        b[2][j] = __float2bfloat16_rn(r - __bfloat162float(b[1][j]));
-      }
-      __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(p.C) + off0;
-#pragma unroll
-      for (int q = 0; q < 3; ++q) {
-        if (q >= p.out_planes) break;
-        uint4* d = reinterpret_cast<uint4*>(c + q * p.out_plane_stride);
-        d[0] = *reinterpret_cast<const uint4*>(&b[q][0]);
-        d[1] = *reinterpret_cast<const uint4*>(&b[q][8]);
-      }
-      return;
-    }
+  // vector stores need the 16-byte alignment of the actual address
+  const bool c16 = (reinterpret_cast<uintptr_t>(p.C) & 15) == 0;
+  if (contig && c16 && off0 >= 0 && off0 + 15 < p.c_lim && !p.accumulate) {
     if (p.out_mode == kOutF32 && (off0 & 3) == 0) {
       float4* d = reinterpret_cast<float4*>(reinterpret_cast<float*>(p.C) + off0);
 #pragma unroll
@@ -288,21 +338,12 @@ __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff
       double* c = reinterpret_cast<double*>(p.C) + off;
       if (p.accumulate) v += *c;
       *c = v;
-    } else {
-      __nv_bfloat16* c = reinterpret_cast<__nv_bfloat16*>(p.C) + off;
-      float h = p.alpha * hi[j], l = p.alpha * lo[j];
-      __nv_bfloat16 b0 = __float2bfloat16_rn(h);
-      float r = (h - __bfloat162float(b0)) + l;
-      c[0] = b0;
-      if (p.out_planes > 1) {
-        __nv_bfloat16 b1 = __float2bfloat16_rn(r);
-        c[p.out_plane_stride] = b1;
-        if (p.out_planes > 2) c[2 * p.out_plane_stride] = __float2bfloat16_rn(r - __bfloat162float(b1));
-      }
     }
   }
 }
 
+// 320 threads: 10 warps, 3 on two of the SM's four sub-partitions, so at most
+// 168 registers a thread (3 x 32 x 168 <= 16384).
 template <int BN, int NP, int BK>
 __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
@@ -311,10 +352,13 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kStages * C::kStage);
-  long long* cn_s = reinterpret_cast<long long*>(bars + C::kBars);
-  int* cv_s = reinterpret_cast<int*>(cn_s + BN);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(cv_s + BN / 16);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + C::kOffBars);
+  long long* cn_s = reinterpret_cast<long long*>(smem + C::kOffCn);
+  int* cv_s = reinterpret_cast<int*>(smem + C::kOffCv);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + C::kOffTmem);
+  long long* xo_s = reinterpret_cast<long long*>(smem + C::kOffXo);
+  float* xm_s = reinterpret_cast<float*>(smem + C::kOffXm);
+  uint8_t* stg_s = smem + C::kOffStg;
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int kProducer = C::kEpiWarps, kMma = C::kEpiWarps + 1;
@@ -374,7 +418,8 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
       uint32_t last_par[C::kStages];
       for (int i = 0; i < C::kStages; ++i) { issued[i] = 0; last_par[i] = 0; }
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-        const int mt = (int)(t / NT), nt = (int)(t % NT);
+        int mt, nt;
+        tile_coords(t, MT, NT, p.m_fast, mt, nt);
         for (int kb = 0; kb < KB; ++kb) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err)) { ok = false; break; }
           mbar_expect_tx(full_bar(s), C::kStage);
@@ -450,7 +495,8 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     float rhi[C::kCols], rlo[C::kCols];
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
-      const int mt = (int)(t / NT), nt = (int)(t % NT);
+      int mt, nt;
+      tile_coords(t, MT, NT, p.m_fast, mt, nt);
       const int m0 = mt * BM, n0 = nt * BN;
       const int m = m0 + row;
       const bool mok = m < p.M;
@@ -462,25 +508,27 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
         tc_fence_after();
         const uint32_t thh = lane_base + (uint32_t)(acc * 2 * BN + col0);
         const uint32_t trs = thh + BN;
+        // 8 columns at a time keeps the live registers (the 2 x kCols running
+        // sums plus the loaded chunk) under the 168-register budget
 #pragma unroll
-        for (int g = 0; g < C::kCols / 16; ++g) {
-          float a[16], b[16];
-          tmem_ld16(thh + g * 16, a);
-          tmem_ld16(trs + g * 16, b);
+        for (int g = 0; g < C::kCols / 8; ++g) {
+          float a[8], b[8];
+          tmem_ld8(thh + g * 8, a);
+          tmem_ld8(trs + g * 8, b);
           tmem_ld_wait();
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
+          for (int j = 0; j < 8; ++j) {
             float s, e;
             two_sum(a[j], b[j], s, e);
             if (c == 0) {
-              rhi[g * 16 + j] = s;
-              rlo[g * 16 + j] = e;
+              rhi[g * 8 + j] = s;
+              rlo[g * 8 + j] = e;
             } else {
               float u, f;
-              two_sum(rhi[g * 16 + j], s, u, f);
-              f += rlo[g * 16 + j] + e;
-              rhi[g * 16 + j] = u + f;
-              rlo[g * 16 + j] = f - (rhi[g * 16 + j] - u);
+              two_sum(rhi[g * 8 + j], s, u, f);
+              f += rlo[g * 8 + j] + e;
+              rhi[g * 8 + j] = u + f;
+              rlo[g * 8 + j] = f - (rhi[g * 8 + j] - u);
             }
           }
         }
@@ -503,11 +551,120 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
         cv_s[threadIdx.x] = okc;
       }
       named_bar(1, kEpiThreads);
-      if (mok) {
+      if (p.out_mode == kOutGridSplit) {
+        // value as the FP32 output would hold it, and this thread's run start
+        float mx = 0.f;
+#pragma unroll
+        for (int j = 0; j < C::kCols; ++j) {
+          rhi[j] = p.alpha * (rhi[j] + rlo[j]);
+          mx = fmaxf(mx, fabsf(rhi[j]));
+        }
+        long long o = -1;
+        if (mok) {
+          o = coff + cn_s[col0];
+          bool run = (o & 63) == 0 && o >= 0 && o + C::kCols <= p.c_lim;
+#pragma unroll
+          for (int g = 0; g < C::kCols / 16; ++g)
+            run = run && cv_s[col0 / 16 + g] && cn_s[col0 + 16 * g] == cn_s[col0] + 16 * g;
+          if (!run) o = -1;
+        }
+        xm_s[half * BM + row] = mx;
+        xo_s[half * BM + row] = o;
+        named_bar(1, kEpiThreads);
+        const int pidx = (half ^ p.seg_phalf) * BM + (row ^ p.seg_prow);
+        const float pm = xm_s[pidx];
+        const long long po = xo_s[pidx];
+        const bool valid = mok && o >= 0 && po == (o ^ 64);
+        if (mok && !valid) report_error(p.err, kErrBounds);
+        // grid of the segment (the rule of kernels.cu: grid_split); v / g is
+        // taken as v * (1/g), the same exactly rounded value (g a power of 2)
+        const float smax = fmaxf(mx, pm);
+        int e = 0;
+        frexpf(smax, &e);
+        const int ge = max(e - 8, -126);
+        const float gq = (smax > 0.f) ? ldexpf(1.f, ge) : 1.f;
+        const float gi = (smax > 0.f) ? ldexpf(1.f, -ge) : 1.f;
+        const bool coop = __all_sync(0xffffffffu, valid);
+        __nv_bfloat16* dst = reinterpret_cast<__nv_bfloat16*>(p.C) + (valid ? o : 0);
+        uint8_t* stage = stg_s + warp * C::kStageBytes;
+        // plane by plane, 32 columns at a time: rhi holds the remainder still
+        // to be split (v, then v - plane0, then v - plane0 - plane1)
+#pragma unroll
+        for (int hh = 0; hh < C::kCols / 32; ++hh) {
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            uint32_t pk[16];
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              __nv_bfloat16 b[2];
+#pragma unroll
+              for (int t = 0; t < 2; ++t) {
+                float& v = rhi[hh * 32 + 2 * i + t];
+                b[t] = (q == 0) ? __float2bfloat16_rn(rintf(v * gi) * gq) : __float2bfloat16_rn(v);
+                v = v - __bfloat162float(b[t]);
+              }
+              pk[i] = pack_bf16x2(b[0], b[1]);
+            }
+            uint4 v4[4];
+#pragma unroll
+            for (int c = 0; c < 4; ++c)
+              v4[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
+            char* d = reinterpret_cast<char*>(dst + q * p.out_plane_stride + hh * 32);
+            if (coop) {
+              warp_store64(stage, v4, d, lane);
+            } else if (valid) {
+#pragma unroll
+              for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(d)[c] = v4[c];
+            }
+          }
+        }
+      } else {
+        // FP32 / FP64 output: 64-byte runs (16 floats or 8 doubles) through the
+        // warp's staging buffer when every lane's run is contiguous and aligned
+        uint8_t* stage = stg_s + warp * C::kStageBytes;
 #pragma unroll
         for (int g = 0; g < C::kCols / 16; ++g) {
           const int cc = col0 + g * 16;
-          store_tile_chunk<BN, NP>(p, coff, cn_s, cv_s[cc / 16], cc, rhi + g * 16, rlo + g * 16);
+          const long long off0 = coff + cn_s[cc];
+          const float* hi = rhi + g * 16;
+          const float* lo = rlo + g * 16;
+          const bool f32 = p.out_mode == kOutF32;
+          const bool run = mok && cv_s[cc / 16] && !p.accumulate && off0 >= 0 &&
+                           off0 + 15 < p.c_lim && (off0 & (f32 ? 3 : 1)) == 0 &&
+                           (reinterpret_cast<uintptr_t>(p.C) & 15) == 0;
+          if (__all_sync(0xffffffffu, run)) {
+            if (f32) {
+              uint4 v4[4];
+#pragma unroll
+              for (int c = 0; c < 4; ++c)
+                v4[c] = make_uint4(__float_as_uint(p.alpha * (hi[4 * c] + lo[4 * c])),
+                                   __float_as_uint(p.alpha * (hi[4 * c + 1] + lo[4 * c + 1])),
+                                   __float_as_uint(p.alpha * (hi[4 * c + 2] + lo[4 * c + 2])),
+                                   __float_as_uint(p.alpha * (hi[4 * c + 3] + lo[4 * c + 3])));
+              warp_store64(stage, v4, reinterpret_cast<char*>(reinterpret_cast<float*>(p.C) + off0),
+                           lane);
+            } else {
+#pragma unroll
+              for (int hv = 0; hv < 2; ++hv) {
+                uint4 v4[4];
+#pragma unroll
+                for (int c = 0; c < 4; ++c) {
+                  const int j = hv * 8 + 2 * c;
+                  const double d0 = (double)p.alpha * ((double)hi[j] + (double)lo[j]);
+                  const double d1 = (double)p.alpha * ((double)hi[j + 1] + (double)lo[j + 1]);
+                  const unsigned long long u0 = __double_as_longlong(d0),
+                                           u1 = __double_as_longlong(d1);
+                  v4[c] = make_uint4((uint32_t)u0, (uint32_t)(u0 >> 32), (uint32_t)u1,
+                                     (uint32_t)(u1 >> 32));
+                }
+                warp_store64(
+                    stage, v4,
+                    reinterpret_cast<char*>(reinterpret_cast<double*>(p.C) + off0 + hv * 8), lane);
+              }
+            }
+          } else if (mok) {
+            store_tile_chunk<BN, NP>(p, coff, cn_s, cv_s[cc / 16], cc, hi, lo);
+          }
         }
       }
     }
@@ -625,6 +782,12 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
       g.pb[0] != 0)
     return cudaErrorInvalidValue;
   if ((reinterpret_cast<uintptr_t>(A.ptr) | reinterpret_cast<uintptr_t>(B.ptr)) & 15)
+    return cudaErrorInvalidValue;
+  if (g.out_mode == kOutGridSplit &&
+      (g.N <= 64 || g.M % BM != 0 || g.N % 128 != 0 || g.out_planes != 3 || g.accumulate ||
+       g.seg_prow < 0 || g.seg_prow >= BM || g.seg_phalf < 0 || g.seg_phalf > 1 ||
+       (g.seg_prow == 0 && g.seg_phalf == 0) || g.out_plane_stride % 64 != 0 ||
+       (reinterpret_cast<uintptr_t>(g.C) & 15) != 0))
     return cudaErrorInvalidValue;
   // K slab: 64 (two 96 KB stages) for two and three planes, where it measured
   // faster (48.1 vs 57.4 ms per D = 64 stage-2 launch); 32 (three 64 KB stages)

@@ -12,7 +12,14 @@ struct TcOperand {
   long long plane_stride;   // elements between planes (>= rows * K)
 };
 
-enum TcOutMode : int { kOutF32 = 0, kOutF64 = 1, kOutSplit = 2 };
+// kOutGridSplit: the tile is written as grid-aligned bf16 planes (the split
+// the next GEMM reads, see kernels.cu: grid_split) of alpha * sum rounded to
+// FP32, bit for bit what kOutF32 followed by grid_split would produce.  Each
+// epilogue thread holds 64 consecutive columns of one row; they must map to 64
+// contiguous destination elements, and together with the 64 of its partner
+// (row ^ seg_prow, column half ^ seg_phalf) fill one aligned 128-element
+// segment of the destination (checked on the device: kErrBounds otherwise).
+enum TcOutMode : int { kOutF32 = 0, kOutF64 = 1, kOutGridSplit = 2 };
 
 struct TcGemm {
   int M, N, K;
@@ -23,7 +30,7 @@ struct TcGemm {
                              // in compensated float-float; >= ceil(K/64) means one chunk
   IMap cm, cn;               // output element (m, n) at C + cm(m) + cn(n)
   int out_mode;              // TcOutMode
-  int out_planes;            // planes written for kOutSplit
+  int out_planes;            // planes written for kOutGridSplit (3)
   long long out_plane_stride;
   void* C;
   float alpha;               // output = alpha * sum
@@ -33,6 +40,9 @@ struct TcGemm {
   int* err;                  // device error word
   int bk;                    // K slab per pipeline stage: 32 or 64 (0: 64 for two or three
                              // planes, 32 for four)
+  int m_fast;                // tile order: 1 = consecutive tiles walk M (B tile reused from
+                             // L2 by neighbouring CTAs), 0 = consecutive tiles walk N
+  int seg_prow, seg_phalf;   // kOutGridSplit: segment partner of (row, half)
 };
 
 // Set the products of a precision: all plane pairs (i, j) with

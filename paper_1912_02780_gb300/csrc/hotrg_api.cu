@@ -289,7 +289,7 @@ TcGemm tcg(const hotrg_plan p, int np, int M, int N, int K, IMap cm, IMap cn, in
   g.alpha = 1.f;
   g.accumulate = 0;
   g.c_lim = lim_of(p, C, mode == kOutF64 ? 8 : (mode == kOutF32 ? 4 : 2));
-  if (mode == kOutSplit && out_plane_stride > 0 && g.c_lim > out_plane_stride)
+  if (mode == kOutGridSplit && out_plane_stride > 0 && g.c_lim > out_plane_stride)
     g.c_lim = out_plane_stride;
   g.err = p->err;
   return g;
@@ -409,6 +409,21 @@ hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, cons
   return HOTRG_OK;
 }
 
+// Segment partner of the grid-split epilogue (see gemm_tc.h: kOutGridSplit)
+// for an output whose 64-column half-runs are `run` consecutive destination
+// elements of the consumer's K: the other half of a 128-segment is in the
+// partner half of the same row (run = 128) or in the row `row_step` away
+// (run = 64).  Returns false when the layout does not allow the fused split.
+bool seg_partner(int run, long long row_step, int& prow, int& phalf) {
+  prow = phalf = 0;
+  if (run == 128) { phalf = 1; return true; }
+  if (run == 64 && row_step > 0 && row_step < 128 && (row_step & (row_step - 1)) == 0) {
+    prow = (int)row_step;
+    return true;
+  }
+  return false;
+}
+
 hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, const double* Ek,
                             double* Tout) {
   const int X = s.X, Y = s.Y, Xp = s.Xp, np = s.np;
@@ -427,26 +442,41 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
   const TcOperand w1 = opnd(p->pW1, Xp * X, X, np, sW1);
   const TcOperand pp = opnd(p->pP, Y * X, X * Y, np, sT);
   const TcOperand w3 = opnd(p->pW3, Xp, X * X, np, sW3);
+  // Three-plane steps write U and V as bf16 planes straight from the GEMM
+  // epilogue where the layout allows it (bit-identical to the FP32 staging
+  // buffer + grid split; saves their FP32 round trip through HBM).
+  const bool fuse = np == 3 && p->cfg.epilogue_split != 0;
+  int p1r = 0, p1h = 0, p2r = 0, p2h = 0;
+  const bool fuse1 = fuse && (Xp * X) % 128 == 0 && (XY % 128) == 0 && X % 2 == 0 &&
+                     seg_partner(Y, 1, p1r, p1h);            // S1: j runs, x2 partner = row ^ 1
+  const bool fuse2 = fuse && (Y * X) % 128 == 0 && (X2 % 128) == 0 &&
+                     seg_partner(X, Xp, p2r, p2h);           // S2: x2' runs, x1' partner = row ^ Xp
   for (int y0 = 0; y0 < Y; y0 += s.ycs) {
     const int yc = (Y - y0) < s.ycs ? (Y - y0) : s.ycs;
     const TcOperand t1 = opnd(p->pT1 + (long long)y0 * X * Y * X, yc * X * Y, X, np, sT);
     {
     Stage sc(p, kStS1);
-    CK(tc_gemm(w1, t1,
-               tcg(p, np, Xp * X, yc * X * Y, X, map2(X, Y, XY),
-                   map3(Y, X, 1, Xp * XY, X * Xp * XY), stage_mode(np), stage_buf(p, np), 0),
-               st, p->sms));
-    CK(fsplit(p, np, yc * X * Xp, X * Y, sC, p->pU));
+    TcGemm g1 = tcg(p, np, Xp * X, yc * X * Y, X, map2(X, Y, XY),
+                    map3(Y, X, 1, Xp * XY, X * Xp * XY),
+                    fuse1 ? kOutGridSplit : stage_mode(np), fuse1 ? (void*)p->pU : stage_buf(p, np),
+                    fuse1 ? sC : 0);
+    g1.m_fast = 1;   // the W1 tiles stay in L2; each T1 tile is read from HBM once
+    g1.seg_prow = p1r;
+    g1.seg_phalf = p1h;
+    CK(tc_gemm(w1, t1, g1, st, p->sms));
+    if (!fuse1) CK(fsplit(p, np, yc * X * Xp, X * Y, sC, p->pU));
     }
     const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
     {
     Stage sc(p, np == 4 ? kStS2Hi : kStS2);
-    CK(tc_gemm(u, pp,
-               tcg(p, np, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
-                   map2(X, 1, X2), stage_mode(np), stage_buf(p, np), 0),
-               st, p->sms));
+    TcGemm g2 = tcg(p, np, yc * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
+                    map2(X, 1, X2), fuse2 ? kOutGridSplit : stage_mode(np),
+                    fuse2 ? (void*)p->pV : stage_buf(p, np), fuse2 ? sC : 0);
+    g2.seg_prow = p2r;
+    g2.seg_phalf = p2h;
+    CK(tc_gemm(u, pp, g2, st, p->sms));
     }
-    {
+    if (!fuse2) {
     Stage sc(p, kStPrep);
     CK(fsplit(p, np, yc * Xp * Y, X * X, sC, p->pV));
     }
@@ -905,6 +935,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_mode = 0;
   c->eigh_power_iters = 4;
   c->eigh_block = 0;
+  c->epilogue_split = 1;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {

@@ -126,13 +126,15 @@ __global__ void __launch_bounds__(256, sizeof(SrcT) == 4 ? 4 : 3)
       // get a coarser grid, which keeps the plane-0 integers even smaller)
       int e = 0;
       frexpf(mx, &e);
-      const float g = (mx > 0.f) ? ldexpf(1.f, max(e - 8, -126)) : 1.f;
+      const int ge = max(e - 8, -126);
+      const float g = (mx > 0.f) ? ldexpf(1.f, ge) : 1.f;
+      const float gi = (mx > 0.f) ? ldexpf(1.f, -ge) : 1.f;   // v / g == v * gi exactly
       if (!active[s]) continue;
       __nv_bfloat16 b[4][4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
         __nv_bfloat16 b0;
-        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] / g) * g);
+        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] * gi) * g);
         else b0 = __double2bfloat16((double)vd[s][i]);
         b[0][i] = b0;
         if constexpr (sizeof(SrcT) == 4) {

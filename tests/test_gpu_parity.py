@@ -207,19 +207,22 @@ def test_fp64_gradient_against_finite_differences_c3_reduced():
     assert err < 1e-6
 
 
-@pytest.mark.parametrize("seed,iters", [(0, 2), (0, 3), (1, 2)])
-def test_subspace_eigensolver_c4_d64_against_stored_oracle(seed, iters):
+@pytest.mark.parametrize("seed,iters,split_from,hi", [(0, 2, 4, 3), (1, 2, 4, 3), (0, 3, 4, 3),
+                                                      (0, 2, 5, 2), (1, 2, 5, 2)])
+def test_subspace_eigensolver_c4_d64_against_stored_oracle(seed, iters, split_from, hi):
     """Forward with the randomized subspace eigensolver (eigh_mode 1: block
     power iteration on 4 D' vectors + Rayleigh-Ritz) in the benchmark's
-    configuration: still within 1e-9 of the oracle's ln Z / N."""
+    configuration (FP64 steps 1-3, four bf16 planes on steps 4-6, three after)
+    and with FP64 steps 1-4, four planes on 5-6: within 1e-9 of the oracle's
+    ln Z / N."""
     g = _golden(f"c4_d64_s{seed}")
     T0 = synth.random_symmetric_T0(seed, 4)
-    with hot.Plan(4, 64, 30, "bf16x6", split_from_step=5, want_grad=False,
-                  hi_precision_steps=2, eigh_mode=1, eigh_power_iters=iters) as p:
+    with hot.Plan(4, 64, 30, "bf16x6", split_from_step=split_from, want_grad=False,
+                  hi_precision_steps=hi, eigh_mode=1, eigh_power_iters=iters) as p:
         lnz, _, sign = p.forward_tensor(T0)
         tr, _, _ = p.diagnostics()
     err = abs(lnz - g["lnz"])
-    print(f"subspace eigh iters={iters}: |dlnz| = {err:.3e}")
+    print(f"subspace eigh iters={iters} split {split_from}/{hi}: |dlnz| = {err:.3e}")
     assert sign == g["trace_sign"]
     assert err < 1e-9
     assert np.max(np.abs(tr - np.array(g["trunc_err"]))) < 1e-7
@@ -241,3 +244,20 @@ def test_subspace_eigensolver_fp64_close_to_full():
     with hot.Plan(4, 32, 16, "fp64", want_grad=False, eigh_mode=1, eigh_power_iters=6) as p:
         lnz, ln, _ = p.forward_tensor(T0)
     assert abs(lnz - ref["lnz"]) < 1e-10
+
+
+def test_epilogue_split_bit_identical_to_staged_split():
+    """The three-plane steps write the stage-1 and stage-2 outputs as bf16
+    planes from the GEMM epilogue; the result must be bit-identical to the
+    FP32 staging buffer followed by the grid-split kernel (D_cut = 64, where
+    both stages take the fused path)."""
+    T0 = synth.random_symmetric_T0(0, 4)
+    out = []
+    for fused in (True, False):
+        with hot.Plan(4, 64, 12, "bf16x6", split_from_step=5, want_grad=False,
+                      hi_precision_steps=2, eigh_mode=1, eigh_power_iters=2,
+                      epilogue_split=fused) as p:
+            lnz, ln, _ = p.forward_tensor(T0)
+        out.append((lnz, np.array(ln)))
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
