@@ -101,6 +101,10 @@ typedef struct {
                                write their outputs as bf16 planes from the epilogue where
                                the layout allows it; 0 = through an FP32 buffer and a
                                separate split kernel (bit-identical results)               */
+  long long split_chunk_elems; /* split steps: elements per bf16 plane of the y-chunked
+                               stage buffers (the D^5 intermediates; <= 0: 2^30).  Smaller
+                               values make the plan smaller and the stage GEMMs shorter;
+                               results do not depend on it.                               */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -108,7 +112,7 @@ typedef struct hotrg_plan_s* hotrg_plan;
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
- * epilogue_split = 1.
+ * epilogue_split = 1, split_chunk_elems = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 

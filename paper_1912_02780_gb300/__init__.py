@@ -51,7 +51,7 @@ class hotrg_config(ctypes.Structure):
                 ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
                 ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
                 ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int),
-                ("epilogue_split", ctypes.c_int)]
+                ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -155,7 +155,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
                 hi_precision_steps: int = 2, eigh_mode: int = 0,
                 eigh_power_iters: int = 4, eigh_block: int = 0,
-                epilogue_split: bool = True) -> hotrg_config:
+                epilogue_split: bool = True, split_chunk_elems: int = 0) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -169,6 +169,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_power_iters = eigh_power_iters
     c.eigh_block = eigh_block
     c.epilogue_split = int(bool(epilogue_split))
+    c.split_chunk_elems = int(split_chunk_elems)
     return c
 
 
@@ -194,11 +195,11 @@ class Plan:
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
                  gram_split_from_step: int = 0, hi_precision_steps: int = 2,
                  eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0,
-                 epilogue_split: bool = True):
+                 epilogue_split: bool = True, split_chunk_elems: int = 0):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
-                               epilogue_split)
+                               epilogue_split, split_chunk_elems)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

@@ -89,7 +89,8 @@ bool build_layout(const hotrg_config& c, Layout& L) {
     long long per_y = X * X * Xp * Y;
     long long a = kChunkF64 / per_y;
     s.yc64 = (int)(a < 1 ? 1 : (a > Y ? Y : a));
-    long long b = kChunkSplit / per_y;
+    const long long chunk_split = c.split_chunk_elems > 0 ? c.split_chunk_elems : kChunkSplit;
+    long long b = chunk_split / per_y;
     s.ycs = (int)(b < 1 ? 1 : (b > Y ? Y : b));
     if (s.N > (1LL << 31) / 2 || X * X * Y * Y > (1LL << 31) || per_y * Y > (1LL << 42)) return false;
     L.g.push_back(s);
@@ -252,6 +253,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->precision < HOTRG_FP64 || c->precision > HOTRG_BF16X6) return HOTRG_EINVAL;
   if (c->split_from_step < 1 || c->hi_precision_steps < 0) return HOTRG_EINVAL;
   if (c->eigh_mode < 0 || c->eigh_mode > 1) return HOTRG_EINVAL;
+  if (c->split_chunk_elems < 0 || c->split_chunk_elems > (1LL << 34)) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -936,6 +938,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_power_iters = 4;
   c->eigh_block = 0;
   c->epilogue_split = 1;
+  c->split_chunk_elems = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {

@@ -64,3 +64,15 @@ def test_status_strings(hot):
     L = hot.lib()
     assert L.hotrg_status_string(0) == b"ok"
     assert L.hotrg_status_string(6) == b"device wait timed out"
+
+
+def test_split_chunk_budget_shrinks_the_plan(hot):
+    kw = dict(precision="bf16x6", split_from_step=4, want_grad=False, hi_precision_steps=3,
+              eigh_mode=1, eigh_power_iters=2)
+    full = hot.workspace_bytes(4, 64, 7, **kw)
+    small = hot.workspace_bytes(4, 64, 7, split_chunk_elems=1 << 26, **kw)
+    assert small < full / 4          # the y-chunked D^5 stage buffers dominate at D_cut = 64
+    L = hot.lib()
+    c = hot.make_config(4, 64, 7, split_chunk_elems=-1, **kw)
+    out = ctypes.c_size_t(0)
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1

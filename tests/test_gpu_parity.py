@@ -253,11 +253,14 @@ def test_epilogue_split_bit_identical_to_staged_split():
     both stages take the fused path)."""
     T0 = synth.random_symmetric_T0(0, 4)
     out = []
-    for fused in (True, False):
+    # fused, staged, and fused with y-chunks of 1/16 (the stage GEMMs split
+    # along M only: every output element is summed in the same order)
+    for fused, chunk in ((True, 0), (False, 0), (True, 1 << 26)):
         with hot.Plan(4, 64, 12, "bf16x6", split_from_step=5, want_grad=False,
                       hi_precision_steps=2, eigh_mode=1, eigh_power_iters=2,
-                      epilogue_split=fused) as p:
+                      epilogue_split=fused, split_chunk_elems=chunk) as p:
             lnz, ln, _ = p.forward_tensor(T0)
         out.append((lnz, np.array(ln)))
-    assert out[0][0] == out[1][0]
-    assert np.array_equal(out[0][1], out[1][1])
+    for o in out[1:]:
+        assert o[0] == out[0][0]
+        assert np.array_equal(o[1], out[0][1])
