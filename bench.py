@@ -9,7 +9,7 @@ hi*hi accumulation), the eigensolve (randomized subspace iteration with
 Rayleigh-Ritz, or cuSOLVER's partial solver), norms and log-norm accumulation
 in FP64;
 steps before --split-from run entirely in FP64.  One benchmark step = the
-solves of the --concurrent seeds (default 1: seed 0), each on its own stream
+solves of the --concurrent seeds (default 2: seeds 0 and 1), each on its own stream
 and host thread (forward; with --grad also the backward).
 
 Printed: one JSON line (rank 0) with solves/s over all GPUs, useful and
@@ -87,11 +87,11 @@ def products_of_step(k, split_from, hi_steps, precision):
 # dram__bytes_write.sum) of the tensor-core GEMM source with this SHA-256; the
 # value is reported only while csrc/gemm_tc.cu is unchanged since the capture.
 STAGE2_TRAFFIC = {
-    "gemm_tc_sha256": "9d9572165621fead03f8f44b064e242ac0a52febde80b3cca80de778a17cab23",
-    # D = 32 capture: 207.9 MB read + 99.6 MB written per stage-2 launch; the
-    # operand and output bytes grow as D^5, so x (64/32)^5 = 32 for D = 64
-    "bytes_per_launch_d64": (207.932416e6 + 99.619328e6) * 32,
-    "captured": "profiles/tc_gemm_stage2_c4_d32_d64.md"}
+    "gemm_tc_sha256": "27ea346c501e6400436fee2a1060ae2bd1c53c9f369183d54dfa5ff6875c3ce6",
+    # full-size D = 64 three-plane stage-2 launch (step 7 of the benchmark's
+    # solve), one-pass ncu capture: 128.11 GB read + 8.26 GB written
+    "bytes_per_launch_d64": 128.11e9 + 8.26e9,
+    "captured": "profiles/tc_gemm_stage2_c4_d64.md"}
 
 
 def gemm_source_sha():
@@ -283,11 +283,17 @@ def main():
     ap.add_argument("--power-iters", type=int, default=2)
     ap.add_argument("--eigh-block", type=int, default=0,
                     help="vectors in the subspace eigensolver's block (0: 4 D_cut)")
-    ap.add_argument("--concurrent", type=int, default=1,
-                    help="independent solves (seeds) per GPU per step, run concurrently "
-                         "(5 measured 0.130 vs 0.121 solves/s for 1 at D_cut = 64: the FP64 "
-                         "eigensolve does not overlap across streams)")
+    ap.add_argument("--concurrent", type=int, default=2,
+                    help="independent solves (seeds) per GPU per step, each on its own "
+                         "stream, so that one solve's latency-bound FP64 eigensolve overlaps "
+                         "the other's tensor-core stages (D_cut = 64: 1 / 2 / 3 / 4 gave "
+                         "0.431 / 0.485 / 0.500 / 0.504 solves/s)")
     ap.add_argument("--grad", type=int, default=0, help="1: each step is forward + backward")
+    ap.add_argument("--n-steps", type=int, default=0,
+                    help="override the workload's coarse-graining steps (profiling runs)")
+    ap.add_argument("--split-chunk", type=int, default=0,
+                    help="elements per plane of the split stage buffers (0: the library's "
+                         "default; smaller = smaller plans and stage GEMMs, same results)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true",
@@ -319,6 +325,11 @@ def main():
     torch.cuda.set_device(dev)
 
     d0, d_cut, n, desc = WORKLOADS[args.workload]
+    full_workload = True
+    if args.n_steps and args.n_steps != n:
+        # a shortened solve (profiling captures): no stored oracle value applies
+        n, full_workload = args.n_steps, False
+        desc += f" (shortened to {n} steps)"
     C = max(1, args.concurrent)
     # this rank's seeds (replicas on N GPUs take disjoint seed blocks)
     seeds = [rank * C + i for i in range(C)]
@@ -327,7 +338,8 @@ def main():
     plans = [hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
                       want_grad=bool(args.grad), stream=st.cuda_stream,
                       hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
-                      eigh_power_iters=args.power_iters, eigh_block=args.eigh_block)
+                      eigh_power_iters=args.power_iters, eigh_block=args.eigh_block,
+                      split_chunk_elems=args.split_chunk)
              for st in streams]
     T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
     out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]
@@ -441,6 +453,7 @@ def main():
             "config": {"workload": args.workload, "desc": desc, "d0": d0, "d_cut": d_cut,
                        "n_steps": n, "precision": args.precision,
                        "split_from_step": args.split_from, "hi_precision_steps": args.hi_steps,
+                       "split_chunk_elems": args.split_chunk or "default (2^30)",
                        "eigh": ("randomized subspace, block %d, %d power iterations"
                                 % (args.eigh_block or 4 * d_cut, args.power_iters)
                                 if args.eigh_mode == 1 else "cuSOLVER syevdx (top D'+1)"),
@@ -457,7 +470,7 @@ def main():
             "clocks": clocks}
     if roof:
         line["roofline"] = roof
-    if rank == 0 and not args.grad:
+    if rank == 0 and not args.grad and full_workload:
         errs = {}
         for sd, lz in zip(seeds, lnzs):
             g = golden(f"{args.workload}_s{sd}")
