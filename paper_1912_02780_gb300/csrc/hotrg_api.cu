@@ -507,20 +507,22 @@ bool subspace_applies(const hotrg_config& c, const StepGeom& s) {
 
 bool use_subspace(const hotrg_plan p, const StepGeom& s) { return subspace_applies(p->cfg, s); }
 
+// Ritz pairs the subspace eigensolver returns: the D' kept and one more.
+int subspace_ritz(const StepGeom& s) { return s.Xp + 1; }
+
 // Randomized subspace eigensolver for the leading eigenpairs of the symmetric
 // PSD Gram matrix G (N x N, in p->Escr): a block of k vectors (eigh_block,
-// default 4 D'), started
-// from a deterministic pseudo-random block, is multiplied by G
-// eigh_power_iters times with a Householder QR (cuSOLVER geqrf + orgqr) after
-// each product, and the Rayleigh-Ritz problem Q^T G Q (k x k, cuSOLVER syevd)
-// gives the Ritz pairs.  The random start is not orthonormalised: only the span
+// default 4 D'), started from a deterministic pseudo-random block, is
+// multiplied by G eigh_power_iters times with a Householder QR (cuSOLVER
+// geqrf + orgqr) after each product, and the Rayleigh-Ritz problem Q^T G Q
+// (k x k, cuSOLVER syevdx, the D' + 1 largest pairs) gives the Ritz pairs.  The random start is not orthonormalised: only the span
 // of the block matters to the iteration.  On split steps the products G Q run
 // on the tensor cores with four-plane operands (10 products, G split once per
 // step, FP64 output); the QR, the projection Q^T (G Q), the small eigensolve and
 // the Ritz vectors stay in FP64.  The block is stored as k contiguous vectors
-// of length N, i.e. an N x k column-major matrix for cuSOLVER.  Output: the k
-// Ritz vectors (ascending Ritz values) in p->Zs as contiguous rows and the Ritz
-// values in p->wasc, ready for eig_desc.
+// of length N, i.e. an N x k column-major matrix for cuSOLVER.  Output: the
+// D' + 1 leading Ritz vectors (ascending Ritz values) in p->Zs as contiguous
+// rows and their Ritz values in p->wasc, ready for eig_desc.
 constexpr int kEighPlanes = 4;
 
 bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
@@ -586,13 +588,18 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
   CK(gemm_f64(g64(p, p->Qs, map_lin(N), map_lin(1), p->Zs, map_lin(N), map_lin(1), p->Hs,
                   map_lin(K), map_lin(1), K, K, N, 1.0, 0.0),
               st, p->sms));
-  if (cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, K, p->Hs, K,
-                       p->wasc, p->swork, p->lswork, p->info) != CUSOLVER_STATUS_SUCCESS)
-    return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd (Rayleigh-Ritz) failed");
+  // only the D' + 1 largest Ritz pairs are used (D' kept, one more for the gap)
+  const int nr = subspace_ritz(s);
+  int meig = 0;
+  if (cusolverDnDsyevdx(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                        CUBLAS_FILL_MODE_LOWER, K, p->Hs, K, 0.0, 0.0, K - nr + 1, K, &meig,
+                        p->wasc, p->swork, p->lswork, p->info) != CUSOLVER_STATUS_SUCCESS ||
+      meig != nr)
+    return fail(p, HOTRG_ECUDA, "cusolverDnDsyevdx (Rayleigh-Ritz) failed");
   CK(eigh_info_check(p->info, p->err, st));
-  // Ritz vectors as rows: V[c][i] = sum_a S[a][c] Q[a][i]  (S column-major K x K)
+  // Ritz vectors as rows: V[c][i] = sum_a S[a][c] Q[a][i]  (S column-major, first nr columns)
   CK(gemm_f64(g64(p, p->Hs, map_lin(K), map_lin(1), p->Qs, map_lin(1), map_lin(N), p->Zs,
-                  map_lin(N), map_lin(1), K, N, K, 1.0, 0.0),
+                  map_lin(N), map_lin(1), nr, N, K, 1.0, 0.0),
               st, p->sms));
   return HOTRG_OK;
 }
@@ -617,7 +624,7 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   if (use_subspace(p, s)) {
     hotrg_status rr = eigh_subspace(p, s, k);
     if (rr != HOTRG_OK) return rr;
-    ncols = subspace_k(p->cfg, s);
+    ncols = subspace_ritz(s);
     evec = p->Zs;
   } else if (p->cfg.want_grad || s.Xp >= N) {
     // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
@@ -1106,15 +1113,17 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       ALC(p->Zs, nmax * kmax);
       ALC(p->Hs, (long long)kmax * kmax);
       ALC(p->tau, kmax);
-      int l1 = 0, l2 = 0, l3 = 0, ls = 0;
+      int l1 = 0, l2 = 0, l3 = 0, ls = 0, meig_q = 0;
       for (const StepGeom& g : L.g) {
         if (!subspace_applies(*cfg, g)) continue;
         const int Kq = subspace_k(*cfg, g), Nq = (int)g.N;
         if (cusolverDnDgeqrf_bufferSize(p->solver, Nq, Kq, p->Qs, Nq, &l1) != CUSOLVER_STATUS_SUCCESS ||
             cusolverDnDorgqr_bufferSize(p->solver, Nq, Kq, Kq, p->Qs, Nq, p->tau, &l2) !=
                 CUSOLVER_STATUS_SUCCESS ||
-            cusolverDnDsyevd_bufferSize(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER,
-                                        Kq, p->Hs, Kq, p->wasc, &l3) != CUSOLVER_STATUS_SUCCESS)
+            cusolverDnDsyevdx_bufferSize(p->solver, CUSOLVER_EIG_MODE_VECTOR, CUSOLVER_EIG_RANGE_I,
+                                         CUBLAS_FILL_MODE_LOWER, Kq, p->Hs, Kq, 0.0, 0.0,
+                                         Kq - subspace_ritz(g) + 1, Kq, &meig_q, p->wasc, &l3) !=
+                CUSOLVER_STATUS_SUCCESS)
           return cleanup(HOTRG_ECUDA);
         ls = std::max(ls, std::max(l1, std::max(l2, l3)));
       }
