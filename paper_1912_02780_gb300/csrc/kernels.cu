@@ -81,6 +81,63 @@ __device__ __forceinline__ void split_load4(const SrcT* __restrict__ src, long l
   }
 }
 
+// The split of one segment: lane holds its 4 consecutive elements vd (zeros
+// when inactive); all 32 lanes take part in the segment-maximum reduction.
+template <typename SrcT>
+__device__ __forceinline__ void split_emit(const SrcT (&vd)[4], bool active, int nplanes,
+                                           int gridded, long long plane_stride,
+                                           __nv_bfloat16* __restrict__ dst, long long obase) {
+  float v[4];
+  float mx = 0.f;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    v[i] = (float)vd[i];
+    mx = fmaxf(mx, fabsf(v[i]));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  // grid 2^(e-8) with 2^(e-1) <= max < 2^e, kept a normal float (tiny segments
+  // get a coarser grid, which keeps the plane-0 integers even smaller)
+  int e = 0;
+  frexpf(mx, &e);
+  const int ge = max(e - 8, -126);
+  const float g = (mx > 0.f) ? ldexpf(1.f, ge) : 1.f;
+  const float gi = (mx > 0.f) ? ldexpf(1.f, -ge) : 1.f;   // v / g == v * gi exactly
+  if (!active) return;
+  __nv_bfloat16 b[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    __nv_bfloat16 b0;
+    if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] * gi) * g);
+    else b0 = __double2bfloat16((double)vd[i]);
+    b[0][i] = b0;
+    if constexpr (sizeof(SrcT) == 4) {
+      // float source: the remainders are exact in float
+      const float rem = v[i] - __bfloat162float(b0);
+      b[1][i] = __float2bfloat16_rn(rem);
+      const float rem2 = rem - __bfloat162float(b[1][i]);
+      b[2][i] = __float2bfloat16_rn(rem2);
+      b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
+    } else {
+      // double source: the first remainder as a float pair keeps the bits a
+      // float would drop (enough for four planes), the rest in float
+      const double remd = (double)vd[i] - (double)__bfloat162float(b0);
+      const float rh = (float)remd;
+      const float rl = (float)(remd - (double)rh);
+      b[1][i] = __float2bfloat16_rn(rh);
+      const float rem2 = (rh - __bfloat162float(b[1][i])) + rl;
+      b[2][i] = __float2bfloat16_rn(rem2);
+      b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
+    }
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q >= nplanes) break;
+    *reinterpret_cast<uint2*>(dst + q * plane_stride + obase) =
+        *reinterpret_cast<const uint2*>(b[q]);
+  }
+}
+
 template <typename SrcT>
 __global__ void __launch_bounds__(256, sizeof(SrcT) == 4 ? 4 : 3)
     grid_split_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm,
@@ -112,57 +169,56 @@ __global__ void __launch_bounds__(256, sizeof(SrcT) == 4 ? 4 : 3)
       }
     }
 #pragma unroll
-    for (int s = 0; s < kSplitSegs; ++s) {
-      float v[4];
-      float mx = 0.f;
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        v[i] = (float)vd[s][i];
-        mx = fmaxf(mx, fabsf(v[i]));
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-      // grid 2^(e-8) with 2^(e-1) <= max < 2^e, kept a normal float (tiny segments
-      // get a coarser grid, which keeps the plane-0 integers even smaller)
-      int e = 0;
-      frexpf(mx, &e);
-      const int ge = max(e - 8, -126);
-      const float g = (mx > 0.f) ? ldexpf(1.f, ge) : 1.f;
-      const float gi = (mx > 0.f) ? ldexpf(1.f, -ge) : 1.f;   // v / g == v * gi exactly
-      if (!active[s]) continue;
-      __nv_bfloat16 b[4][4];
-#pragma unroll
-      for (int i = 0; i < 4; ++i) {
-        __nv_bfloat16 b0;
-        if (gridded) b0 = __float2bfloat16_rn(rintf(v[i] * gi) * g);
-        else b0 = __double2bfloat16((double)vd[s][i]);
-        b[0][i] = b0;
-        if constexpr (sizeof(SrcT) == 4) {
-          // float source: the remainders are exact in float
-          const float rem = v[i] - __bfloat162float(b0);
-          b[1][i] = __float2bfloat16_rn(rem);
-          const float rem2 = rem - __bfloat162float(b[1][i]);
-          b[2][i] = __float2bfloat16_rn(rem2);
-          b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
-        } else {
-          // double source: the first remainder as a float pair keeps the bits a
-          // float would drop (enough for four planes), the rest in float
-          const double remd = (double)vd[s][i] - (double)__bfloat162float(b0);
-          const float rh = (float)remd;
-          const float rl = (float)(remd - (double)rh);
-          b[1][i] = __float2bfloat16_rn(rh);
-          const float rem2 = (rh - __bfloat162float(b[1][i])) + rl;
-          b[2][i] = __float2bfloat16_rn(rem2);
-          b[3][i] = __float2bfloat16_rn(rem2 - __bfloat162float(b[2][i]));
-        }
-      }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        if (q >= nplanes) break;
-        *reinterpret_cast<uint2*>(dst + q * plane_stride + obase[s]) =
-            *reinterpret_cast<const uint2*>(b[q]);
-      }
+    for (int s = 0; s < kSplitSegs; ++s)
+      split_emit(vd[s], active[s], nplanes, gridded, plane_stride, dst, obase[s]);
+  }
+}
+
+// The same split for sources whose rows, not K, are contiguous (the first
+// radix level of the row map has stride 1 and covers whole groups of 32 rows):
+// a block stages 32 rows x one K segment in shared memory, read with
+// consecutive lanes on consecutive rows (coalesced), then splits each row's
+// segment exactly as grid_split_kernel does (same split_emit).
+constexpr int kRowsTile = 32;
+constexpr int kRowsPitch = kGridSeg + 2;   // elements per staged row (segments <= kGridSeg)
+
+// rstep = 1: the tile is 32 consecutive rows; rstep > 1: the unit stride is on
+// the second level (row = i + rstep q), and the tile is 32 consecutive q for
+// one i.
+template <typename SrcT>
+__global__ void __launch_bounds__(256)
+    grid_split_rows_kernel(const SrcT* __restrict__ src, long long src_lim, IMap rm, IMap km,
+                           int rows, int K, int seg, int nplanes, int gridded, int rstep,
+                           long long plane_stride, __nv_bfloat16* __restrict__ dst, int* err) {
+  __shared__ __align__(16) SrcT tile[kRowsTile][kRowsPitch];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nseg = (K + seg - 1) / seg;
+  const long long work = (long long)(rows / kRowsTile) * nseg;
+  for (long long w = blockIdx.x; w < work; w += gridDim.x) {
+    const int rb = (int)(w / nseg), sg = (int)(w % nseg);
+    // first row of the tile and the row of lane l = rfirst + l * rstep
+    const int rfirst = (rstep == 1) ? rb * kRowsTile
+                                    : (rb % rstep) + rstep * (rb / rstep) * kRowsTile;
+    const int k0 = sg * seg;
+    const int kn = min(seg, K - k0);
+    const long long roff = imap(rm, rfirst + lane * rstep);
+    for (int kk = warp; kk < kn; kk += 8) {
+      const long long off = roff + imap(km, k0 + kk);
+      SrcT v = SrcT(0);
+      if (off >= 0 && off < src_lim) v = src[off];
+      else report_error(err, kErrBounds);
+      tile[lane][kk] = v;
     }
+    __syncthreads();
+    for (int i = warp; i < kRowsTile; i += 8) {
+      const bool active = 4 * lane < kn;
+      SrcT vd[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) vd[j] = active ? tile[i][4 * lane + j] : SrcT(0);
+      split_emit(vd, active, nplanes, gridded, plane_stride, dst,
+                 (long long)(rfirst + i * rstep) * K + k0 + 4 * lane);
+    }
+    __syncthreads();
   }
 }
 
@@ -457,12 +513,29 @@ cudaError_t grid_split_t(const SrcT* src, long long src_lim, IMap rm, IMap km, i
   const int gridded = nplanes >= 3 ? 1 : 0;
   if (nplanes < 1 || nplanes > 4 || K % 8 != 0 || plane_stride % 4 != 0)
     return cudaErrorInvalidValue;
-  // contiguous K (single-level unit-stride map): vector loads
-  const int contig = (km.s0 == 1 && km.r0 >= K) ? 1 : 0;
+  // unit stride on K's first radix level, in runs of a multiple of 4: every
+  // lane's 4 elements are contiguous (vector loads)
+  const int contig = (km.s0 == 1 && km.r0 % 4 == 0) ? 1 : 0;
   const int seg = K < kGridSeg ? K : kGridSeg;
   const long long work = (long long)rows * ((K + seg - 1) / seg);
   if (work == 0) return cudaSuccess;
   if ((long long)rows * K > plane_stride) return cudaErrorInvalidValue;
+  // rows contiguous, K strided: stage 32-row tiles through shared memory.
+  // Unit stride on the rows' first level (32 consecutive rows), or on the
+  // second level of a two-level row map (rows i + r0 q, 32 consecutive q).
+  int rstep = 0;
+  if (rm.s0 == 1 && rm.r0 % kRowsTile == 0 && rows % kRowsTile == 0) rstep = 1;
+  else if (rm.r1 == kBig && rm.s1 == 1 && rm.r0 > 1 && rows % rm.r0 == 0 &&
+           (rows / rm.r0) % kRowsTile == 0)
+    rstep = rm.r0;
+  if (!contig && rstep > 0 && seg <= kGridSeg) {
+    long long rblocks = (long long)(rows / kRowsTile) * ((K + seg - 1) / seg);
+    if (rblocks > 8LL * sms) rblocks = 8LL * sms;
+    count_launch();
+    grid_split_rows_kernel<SrcT><<<(int)rblocks, 256, 0, st>>>(
+        src, src_lim, rm, km, rows, K, seg, nplanes, gridded, rstep, plane_stride, dst, err);
+    return cudaGetLastError();
+  }
   long long blocks = (work + 8 * kSplitSegs - 1) / (8 * kSplitSegs);   // 8 warps per block
   if (blocks > 16LL * sms) blocks = 16LL * sms;
   count_launch();

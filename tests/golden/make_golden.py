@@ -12,6 +12,8 @@ Cases:
   c3_bc_h0    Ising at beta_c, h = 0, D_cut = 64, 40 steps (forward)
   c3_bc_h001  Ising at beta_c, h = 0.01, D_cut = 64, 40 steps (forward)
   c2_grid     Ising, 64 betas on [0.30, 0.60], D_cut = 32, 30 steps (forward + d/dbeta)
+  c4_d96_s0_n7  random T0 (d0 = 4, seed 0), D_cut = 96, 7 steps (forward; steps 5-7 at the
+              full D_cut = 96 bond dimensions)
 """
 import json
 import os
@@ -45,6 +47,9 @@ def main(cases):
             seed = int(c[len("c4_d64_s"):])
             fwd_case(c, synth.random_symmetric_T0(seed, 4), 64, 30,
                      dict(model="random reflection-symmetric T0", d0=4, seed=seed))
+        elif c == "c4_d96_s0_n7":
+            fwd_case(c, synth.random_symmetric_T0(0, 4), 96, 7,
+                     dict(model="random reflection-symmetric T0", d0=4, seed=0))
         elif c == "c3_bc_h0":
             fwd_case(c, ising.ising_T0(synth.BETA_C, 1.0, 0.0), 64, 40,
                      dict(model="ising", beta=synth.BETA_C, J=1.0, h=0.0, d0=2))
