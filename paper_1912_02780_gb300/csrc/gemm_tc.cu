@@ -2,24 +2,27 @@
 //
 //   C(m, n) = alpha * sum_k A(m, k) * B(n, k)
 //
-// Both operands are K-major and split into bf16 planes (hi, lo [, lo2]) so
-// that a*b ~= sum over the plane pairs (i, j) with i + j <= nplanes - 1 of
+// Both operands are K-major and split into bf16 planes (hi, lo [, lo2, lo3])
+// so that a*b ~= sum over the plane pairs (i, j) with i + j <= nplanes - 1 of
 // a_i * b_j.  This is how the O(D^7) contractions of the HOTRG step (SM
 // Sec. B, HOTRG step equation) and of its adjoint run at tensor-core rate
-// while keeping about 16 (two planes) or 24 (three planes) significant bits
-// per product.
+// while keeping about 16, 24 or 32 significant bits per product (two, three
+// or four planes).
 //
-// Structure (one persistent CTA per SM, 192 threads):
-//   warp 4      TMA producer: per 64-wide K slab, one 3-D tensor-map load per
-//               operand plane into a 128B-swizzled shared-memory stage.
-//   warp 5      MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16)
-//               for every plane pair and K step; tcgen05.commit frees the
-//               stage and, at the end of an accumulation chunk, hands the
-//               TMEM accumulator (double-buffered) to the epilogue.
-//   warps 0-3   epilogue: tcgen05.ld the accumulator (one TMEM lane per row),
-//               optionally add the chunk into a compensated float-float sum kept
-//               in TMEM, and write the tile through the output index maps as
-//               FP32, FP64 or split bf16 planes.
+// Structure (one persistent CTA per SM, 320 threads):
+//   warp 8      TMA producer: per K slab (64 or 32 wide), one 3-D tensor-map
+//               load per operand plane into a swizzled shared-memory stage.
+//   warp 9      MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16)
+//               for every plane pair and K step, hi*hi into its own exactly
+//               accumulated TMEM buffer, the other products into a second;
+//               tcgen05.commit frees the stage and, at the end of an
+//               accumulation chunk, hands the (double-buffered) accumulators
+//               to the epilogue.
+//   warps 0-7   epilogue: tcgen05.ld the accumulators (one TMEM lane per row,
+//               half the columns per warp), add the chunk into float-float
+//               register sums, and write the tile through the output index
+//               maps as FP32, FP64 or grid-split bf16 planes, staged through a
+//               per-warp shared-memory transpose for whole-sector stores.
 // Every mbarrier wait is bounded; on timeout the error word gets kErrTimeout,
 // the role stops, and all warps still meet at the final barrier, drain their
 // MMAs and free TMEM.
