@@ -105,6 +105,11 @@ typedef struct {
                                stage buffers (the D^5 intermediates; <= 0: 2^30).  Smaller
                                values make the plan smaller and the stage GEMMs shorter;
                                results do not depend on it.                               */
+  int w_given;              /* 1 = the isometries are parameters (differentiable-TRG sweeps,
+                               main text after Eq. (1)): the forward uses the ones loaded
+                               with hotrg_set_isometries or left by hotrg_mera_update and
+                               forms no Gram and no eigensolve.  Needs want_grad = 1 and
+                               fixed_w_grad = 1.                                          */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -112,9 +117,32 @@ typedef struct hotrg_plan_s* hotrg_plan;
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
- * epilogue_split = 1, split_chunk_elems = 0.
+ * epilogue_split = 1, split_chunk_elems = 0, w_given = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
+
+/* Differentiable TRG (main text: SRG as backpropagation, Eq. (1) E_w = wbar / N_i,
+ * and the MERA update of w from the SVD of E_w).  All buffers below are the
+ * isometries of every step, concatenated over k = 1..n_steps; step k holds
+ * X'_k x X_k^2 doubles, row a = the a-th kept vector over (x1 x2), x1 major
+ * (X, X' from hotrg_step_dims).  Host buffers, caller-owned; the calls
+ * synchronise the plan's stream.
+ *
+ * hotrg_isometries: the isometries of the last forward (gradient plans) or
+ *   the ones loaded / updated (w_given plans).
+ * hotrg_set_isometries: load them into a w_given plan (entries must be finite;
+ *   they are used as given, orthonormal or not).
+ * hotrg_isometry_adjoints: d(ln Z/N)/d w_k of the last backward (gradient
+ *   plans): with fixed_w_grad = 1 this is the environment of w_k, E_w = wbar.
+ * hotrg_mera_update(plan, k): after a backward of a w_given plan, replace w_k
+ *   by the isometry maximising Tr(E_w^T w): E_w = U S V^T (cuSOLVER gesvd,
+ *   FP64), w_k = U V^T.  The next forward sees the new w_k.
+ * HOTRG_ESTATE when called out of order (no forward / backward yet, or a plan
+ * without w_given). */
+hotrg_status hotrg_isometries(hotrg_plan plan, double* w);
+hotrg_status hotrg_set_isometries(hotrg_plan plan, const double* w);
+hotrg_status hotrg_isometry_adjoints(hotrg_plan plan, double* wbar);
+hotrg_status hotrg_mera_update(hotrg_plan plan, int step);
 
 /* sizeof(hotrg_config) as compiled into the library, so that a binding can
  * check that its copy of the struct matches. */

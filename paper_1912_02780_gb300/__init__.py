@@ -27,7 +27,8 @@ STATUS = {0: "HOTRG_OK", 1: "HOTRG_EINVAL", 2: "HOTRG_ENOMEM", 3: "HOTRG_ECUDA",
 
 # Every symbol declared in include/hotrg.h.
 EXPORTS = (
-    "hotrg_config_default", "hotrg_config_sizeof", "hotrg_plan_workspace_bytes", "hotrg_plan_create",
+    "hotrg_config_default", "hotrg_config_sizeof", "hotrg_plan_workspace_bytes",
+    "hotrg_isometries", "hotrg_set_isometries", "hotrg_isometry_adjoints", "hotrg_mera_update", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
     "hotrg_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
@@ -51,7 +52,8 @@ class hotrg_config(ctypes.Structure):
                 ("eigh_broadening", ctypes.c_double), ("gram_split_from_step", ctypes.c_int),
                 ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
                 ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int),
-                ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong)]
+                ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong),
+                ("w_given", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -137,6 +139,10 @@ def lib() -> ctypes.CDLL:
                         "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy",
                         "hotrg_config_sizeof"):
             getattr(L, name).restype = ctypes.c_int
+    L.hotrg_isometries.argtypes = [vp, _dp]
+    L.hotrg_set_isometries.argtypes = [vp, _dp]
+    L.hotrg_isometry_adjoints.argtypes = [vp, _dp]
+    L.hotrg_mera_update.argtypes = [vp, ctypes.c_int]
     L.hotrg_config_sizeof.argtypes = []
     L.hotrg_config_sizeof.restype = ctypes.c_size_t
     if L.hotrg_config_sizeof() != ctypes.sizeof(hotrg_config):
@@ -155,7 +161,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 eigh_broadening: float = 1e-12, gram_split_from_step: int = 0,
                 hi_precision_steps: int = 2, eigh_mode: int = 0,
                 eigh_power_iters: int = 4, eigh_block: int = 0,
-                epilogue_split: bool = True, split_chunk_elems: int = 0) -> hotrg_config:
+                epilogue_split: bool = True, split_chunk_elems: int = 0,
+                w_given: bool = False) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -170,6 +177,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_block = eigh_block
     c.epilogue_split = int(bool(epilogue_split))
     c.split_chunk_elems = int(split_chunk_elems)
+    c.w_given = int(bool(w_given))
     return c
 
 
@@ -195,11 +203,12 @@ class Plan:
                  eigh_broadening: float = 1e-12, stream: Optional[int] = None,
                  gram_split_from_step: int = 0, hi_precision_steps: int = 2,
                  eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0,
-                 epilogue_split: bool = True, split_chunk_elems: int = 0):
+                 epilogue_split: bool = True, split_chunk_elems: int = 0,
+                 w_given: bool = False):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
-                               epilogue_split, split_chunk_elems)
+                               epilogue_split, split_chunk_elems, w_given)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))
@@ -254,6 +263,43 @@ class Plan:
         s = np.zeros(self.n_steps, dtype=np.int32)
         self._check(lib().hotrg_diagnostics(self._h, _p(t), _p(g), s.ctypes.data_as(_ip)), "diagnostics")
         return t, g, s
+
+    # ---- differentiable TRG: isometries as parameters ----------------------
+    def _w_layout(self):
+        shapes, off = [], 0
+        for k in range(1, self.n_steps + 1):
+            X, _, Xp = self.step_dims(k)
+            shapes.append((off, Xp, X * X, X))
+            off += Xp * X * X
+        return shapes, off
+
+    def _split_w(self, flat):
+        """Per-step arrays w[x1, x2, a] (the oracle's layout) from the ABI's rows."""
+        shapes, _ = self._w_layout()
+        return [flat[o:o + xp * n].reshape(xp, x, x).transpose(1, 2, 0).copy()
+                for o, xp, n, x in shapes]
+
+    def isometries(self):
+        _, tot = self._w_layout()
+        flat = np.zeros(tot)
+        self._check(lib().hotrg_isometries(self._h, _p(flat)), "isometries")
+        return self._split_w(flat)
+
+    def set_isometries(self, ws):
+        shapes, tot = self._w_layout()
+        flat = np.zeros(tot)
+        for (o, xp, n, x), w in zip(shapes, ws):
+            flat[o:o + xp * n] = np.asarray(w, dtype=np.float64).transpose(2, 0, 1).reshape(-1)
+        self._check(lib().hotrg_set_isometries(self._h, _p(flat)), "set_isometries")
+
+    def isometry_adjoints(self):
+        _, tot = self._w_layout()
+        flat = np.zeros(tot)
+        self._check(lib().hotrg_isometry_adjoints(self._h, _p(flat)), "isometry_adjoints")
+        return self._split_w(flat)
+
+    def mera_update(self, k: int):
+        self._check(lib().hotrg_mera_update(self._h, int(k)), "mera_update")
 
     def step_dims(self, k: int):
         X, Y, Xp = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()

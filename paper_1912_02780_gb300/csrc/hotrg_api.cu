@@ -161,7 +161,14 @@ struct hotrg_plan_s {
   double *Qs = nullptr, *Zs = nullptr, *Hs = nullptr, *tau = nullptr, *swork = nullptr,
          *wsmall = nullptr;
   int kspace = 0, lswork = 0;
-  bool have_fwd = false, fwd_ising = false;
+  bool have_fwd = false, fwd_ising = false, have_bwd = false, w_loaded = false;
+  // gradient plans: d(ln Z/N)/d w_k of every step (rows = kept vectors)
+  double* wbar_all = nullptr;
+  std::vector<long long> w_off;        // offset of step k's Xp x N block
+  // MERA update (SVD of the environment): workspace and status
+  double* svd_work = nullptr;
+  double* svd_rwork = nullptr;
+  int svd_lwork = 0;
   std::string last_error;
   // optional per-stage CUDA-event timing
   bool prof = false;
@@ -254,6 +261,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->split_from_step < 1 || c->hi_precision_steps < 0) return HOTRG_EINVAL;
   if (c->eigh_mode < 0 || c->eigh_mode > 1) return HOTRG_EINVAL;
   if (c->split_chunk_elems < 0 || c->split_chunk_elems > (1LL << 34)) return HOTRG_EINVAL;
+  if (c->w_given && (!c->want_grad || !c->fixed_w_grad)) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -613,6 +621,12 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   double* lk = p->lam[k - 1];
   const int N = (int)s.N;
   hotrg_status r;
+  if (p->cfg.w_given) {
+    // the isometries are parameters (differentiable-TRG sweeps): no Gram, no
+    // eigensolve; truncation diagnostics are not defined
+    CK(set_value(p->dtrunc + (k - 1), std::nan(""), nullptr, 0, st));
+    CK(set_value(p->dgap + (k - 1), std::nan(""), nullptr, 0, st));
+  } else {
   if (s.split && k >= p->cfg.gram_split_from_step) r = gram_split(p, s, T, p->Escr);
   else r = gram_f64(p, s, T, p->Abuf, p->Bbuf, p->Escr);
   if (r != HOTRG_OK) return r;
@@ -648,6 +662,7 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
   CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
   }
+  }
   if (s.split) r = contract_split(p, s, T, Ek, Tout);
   else r = contract_f64(p, s, T, Ek, Tout);
   if (r != HOTRG_OK) return r;
@@ -662,6 +677,9 @@ hotrg_status step_forward(hotrg_plan p, int k) {
 
 hotrg_status run_forward(hotrg_plan p) {
   cudaStream_t st = p->stream;
+  if (p->cfg.w_given && !p->w_loaded)
+    return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
+  p->have_bwd = false;
   for (int k = 1; k <= p->cfg.n_steps; ++k) {
     hotrg_status r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
@@ -814,6 +832,10 @@ hotrg_status step_backward(hotrg_plan p, int k) {
                     map2(Y, Y, XY2), p->Tbar, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y,
                     2.0, 1.0)));
   }
+  // d(ln Z/N)/d w_k = wbT / 2^k (wbT carries the 2^k of E_k)
+  if (p->wbar_all)
+    CK(scale_copy(p->wbT, p->wbar_all + p->w_off[k - 1], (long long)Xp * N, std::ldexp(1.0, -k), st,
+                  p->sms));
   // E_{k-1} = (1/2) Tbar (average of the two copies), in the layout of T_{k-1}
   CK(scale_copy(p->Tbar, p->Enext, X2 * Y2, 0.5, st, p->sms));
   double* tmp = p->Ecur;
@@ -946,6 +968,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_block = 0;
   c->epilogue_split = 1;
   c->split_chunk_elems = 0;
+  c->w_given = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -961,6 +984,9 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
   b.add(L.maxT, 8 * 4);       // Abuf Bbuf Abar Bbar
   b.add(L.chunk64, 8 * 2);    // Ub Vb
   if (c->want_grad) {
+    long long wtot = 0;
+    for (const StepGeom& g : L.g) wtot += (long long)g.Xp * g.N;
+    b.add(wtot, 8);           // per-step isometry adjoints
     b.add(L.chunk64, 8 * 2);  // Pb Qb
     b.add(L.maxN * L.maxXp, 8 * 3);
     b.add(L.maxN2, 8);
@@ -1048,6 +1074,14 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     ALC(p->Hb, L.maxN * L.maxXp);
     ALC(p->wbT, L.maxN * L.maxXp);
     ALC(p->Gb, L.maxN2);
+    {
+      long long tot = 0;
+      for (const StepGeom& g : L.g) {
+        p->w_off.push_back(tot);
+        tot += (long long)g.Xp * g.N;
+      }
+      ALC(p->wbar_all, tot);
+    }
     ALC(p->Ecur, L.maxT);
     ALC(p->Enext, L.maxT);
     ALC(p->Tbar, L.maxT);
@@ -1101,6 +1135,18 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   }
   p->lwork = lw;
   ALC(p->work, (long long)lw);
+  if (cfg->w_given) {
+    int ls = 0;
+    for (const StepGeom& g : L.g) {
+      int l = 0;
+      if (cusolverDnDgesvd_bufferSize(p->solver, (int)g.N, g.Xp, &l) != CUSOLVER_STATUS_SUCCESS)
+        return cleanup(HOTRG_ECUDA);
+      ls = std::max(ls, l);
+    }
+    p->svd_lwork = ls;
+    ALC(p->svd_work, (long long)ls);
+    ALC(p->svd_rwork, L.maxXp);
+  }
   if (cfg->eigh_mode == 1 && !cfg->want_grad) {
     int kmax = 0;
     long long nmax = 0;
@@ -1213,6 +1259,7 @@ hotrg_status hotrg_backward_device(hotrg_plan p, double* grad_dev) {
   CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), p->stream));
   hotrg_status r = run_backward(p);
   if (r != HOTRG_OK) return r;
+  p->have_bwd = true;
   if (grad_dev) {
     const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
     CK(cudaMemcpyAsync(grad_dev, p->Ecur, sizeof(double) * n0, cudaMemcpyDeviceToDevice,
@@ -1260,6 +1307,71 @@ hotrg_status hotrg_step_dims(hotrg_plan p, int step, int* X, int* Y, int* Xp) {
   if (X) *X = g.X;
   if (Y) *Y = g.Y;
   if (Xp) *Xp = g.Xp;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_isometries(hotrg_plan p, double* w) {
+  if (!p || !w) return HOTRG_EINVAL;
+  if (!p->cfg.want_grad) return fail(p, HOTRG_ESTATE, "isometries are kept by gradient plans");
+  if (!p->have_fwd && !p->w_loaded) return fail(p, HOTRG_ESTATE, "no forward yet");
+  for (int k = 1; k <= p->cfg.n_steps; ++k) {
+    const StepGeom& g = p->L.g[k - 1];
+    CK(cudaMemcpyAsync(w + p->w_off[k - 1], p->E[k - 1], sizeof(double) * g.Xp * g.N,
+                       cudaMemcpyDeviceToHost, p->stream));
+  }
+  return finish_sync(p);
+}
+
+hotrg_status hotrg_set_isometries(hotrg_plan p, const double* w) {
+  if (!p || !w) return HOTRG_EINVAL;
+  if (!p->cfg.w_given) return fail(p, HOTRG_ESTATE, "plan created with w_given = 0");
+  for (int k = 1; k <= p->cfg.n_steps; ++k) {
+    const StepGeom& g = p->L.g[k - 1];
+    const long long n = (long long)g.Xp * g.N;
+    for (long long i = 0; i < n; ++i)
+      if (!std::isfinite(w[p->w_off[k - 1] + i]))
+        return fail(p, HOTRG_EINVAL, "isometry entries must be finite");
+    CK(cudaMemcpyAsync(p->E[k - 1], w + p->w_off[k - 1], sizeof(double) * n,
+                       cudaMemcpyHostToDevice, p->stream));
+  }
+  hotrg_status r = finish_sync(p);
+  if (r != HOTRG_OK) return r;
+  p->w_loaded = true;
+  p->have_fwd = p->have_bwd = false;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_isometry_adjoints(hotrg_plan p, double* wbar) {
+  if (!p || !wbar) return HOTRG_EINVAL;
+  if (!p->wbar_all || !p->have_bwd) return fail(p, HOTRG_ESTATE, "needs a backward first");
+  const StepGeom& last = p->L.g.back();
+  const long long tot = p->w_off.back() + (long long)last.Xp * last.N;
+  CK(cudaMemcpyAsync(wbar, p->wbar_all, sizeof(double) * tot, cudaMemcpyDeviceToHost, p->stream));
+  return finish_sync(p);
+}
+
+hotrg_status hotrg_mera_update(hotrg_plan p, int k) {
+  if (!p || k < 1 || k > p->cfg.n_steps) return HOTRG_EINVAL;
+  if (!p->cfg.w_given) return fail(p, HOTRG_ESTATE, "plan created with w_given = 0");
+  if (!p->have_bwd) return fail(p, HOTRG_ESTATE, "the MERA update needs a backward first");
+  const StepGeom& g = p->L.g[k - 1];
+  const int N = (int)g.N, Xp = g.Xp;
+  cudaStream_t st = p->stream;
+  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), st));
+  // E_w (rows = kept vectors) is the N x Xp column-major matrix cuSOLVER reads
+  CK(cudaMemcpyAsync(p->Gb, p->wbar_all + p->w_off[k - 1], sizeof(double) * (size_t)Xp * N,
+                     cudaMemcpyDeviceToDevice, st));
+  if (cusolverDnDgesvd(p->solver, 'S', 'S', N, Xp, p->Gb, N, p->wasc, p->Hb, N, p->Sb, Xp,
+                       p->svd_work, p->svd_lwork, p->svd_rwork, p->info) != CUSOLVER_STATUS_SUCCESS)
+    return fail(p, HOTRG_ECUDA, "cusolverDnDgesvd failed");
+  CK(eigh_info_check(p->info, p->err, st));
+  // w = U V^T: w_k[a][i] = sum_c VT(c, a) U(i, c)   (U: N x Xp, VT: Xp x Xp, column-major)
+  CK(gemm_f64(g64(p, p->Sb, map_lin(Xp), map_lin(1), p->Hb, map_lin(1), map_lin(N), p->E[k - 1],
+                  map_lin(N), map_lin(1), Xp, N, Xp, 1.0, 0.0),
+              st, p->sms));
+  hotrg_status r = finish_sync(p);
+  if (r != HOTRG_OK) return r;
+  p->have_fwd = p->have_bwd = false;     // the network changed
   return HOTRG_OK;
 }
 

@@ -76,3 +76,14 @@ def test_split_chunk_budget_shrinks_the_plan(hot):
     c = hot.make_config(4, 64, 7, split_chunk_elems=-1, **kw)
     out = ctypes.c_size_t(0)
     assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
+
+
+def test_w_given_needs_fixed_w_gradients(hot):
+    L = hot.lib()
+    out = ctypes.c_size_t(0)
+    c = hot.make_config(2, 8, 6, w_given=True)                 # fixed_w_grad = 0
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
+    c = hot.make_config(2, 8, 6, w_given=True, fixed_w_grad=True, want_grad=False)
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
+    c = hot.make_config(2, 8, 6, w_given=True, fixed_w_grad=True)
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 0
