@@ -76,3 +76,24 @@ def test_w_given_plan_needs_isometries_first():
         with pytest.raises(hot.HotrgError) as e2:
             p.mera_update(1)
         assert e2.value.status == 7
+
+
+def test_dtrg_improves_on_hotrg_near_criticality():
+    """Main text Fig. 2 (shape only; the plotted values are not available):
+    free-energy error against Onsager of HOTRG and of dTRG (one sweep, three
+    MERA updates per layer) at D_cut = 24, 30 steps (2^30 sites, finite-size
+    terms far below these errors off criticality), split precision."""
+    from oracle import exact
+    from paper_1912_02780_gb300.dtrg import dtrg_sweeps
+    rows = []
+    for beta in (0.42, float(synth.BETA_C), 0.46):
+        r = dtrg_sweeps(2, 24, 30, n_sweeps=1, n_inner=3, beta=beta, precision="bf16x6",
+                        split_from_step=5)
+        ons = exact.onsager_lnz(beta)
+        e_h = abs(r["lnz_hotrg"] - ons) / abs(ons)
+        e_d = abs(r["lnz_final"] - ons) / abs(ons)
+        rows.append((beta, e_h, e_d))
+        print(f"beta = {beta:.6f}: |df/f| HOTRG {e_h:.3e}, dTRG {e_d:.3e}")
+    for beta, e_h, e_d in rows:
+        if abs(beta - synth.BETA_C) > 1e-3:
+            assert e_d < e_h
