@@ -267,6 +267,42 @@ def run_serve(args):
     print(json.dumps(line), flush=True)
 
 
+def run_grid(args):
+    """The Ising beta grid (64 betas on [0.30, 0.60], D_cut = 32, 30 steps,
+    forward + hand-written adjoint on one reused plan): ln Z/N, f, u and c
+    (second-order finite differences of the adjoint's u), solves/s over the
+    grid, and the largest errors against the oracle's stored grid."""
+    import torch
+    import paper_1912_02780_gb300 as hot  # noqa: F401  (loads the library)
+    from paper_1912_02780_gb300.observables import ising_thermodynamics
+    betas = synth.beta_grid()
+    split = args.precision != "fp64"
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    res = ising_thermodynamics(betas, 32, 30, args.precision,
+                               split_from_step=args.split_from if split else 1,
+                               hi_precision_steps=args.hi_steps)
+    dt = time.perf_counter() - t0
+    line = {"metric": "beta-grid solves/s (forward + backward)", "value": len(betas) / dt,
+            "unit": "solves/s", "higher_is_better": True, "seconds": dt,
+            "dtype": args.precision, "data": "synthetic",
+            "config": {"workload": "c2_grid", "betas": len(betas), "d_cut": 32, "n_steps": 30,
+                       "split_from_step": args.split_from if split else None,
+                       "hi_precision_steps": args.hi_steps if split else None}}
+    g = golden("c2_grid")
+    if g:
+        lnz_ref = np.array([q["lnz"] for q in g["points"]])
+        u_ref = -np.array([q["dlnz_dbeta"] for q in g["points"]])
+        line["max_abs_df_vs_oracle"] = float(np.max(np.abs(res["lnz"] - lnz_ref) / betas))
+        line["max_rel_du_vs_oracle"] = float(np.max(np.abs(res["u"] - u_ref) / np.abs(u_ref)))
+        # the oracle's specific heat by the same finite-difference rule
+        from paper_1912_02780_gb300.observables import grid_derivative
+        c_ref = -betas ** 2 * grid_derivative(betas, u_ref)
+        line["max_rel_dc_vs_oracle"] = float(np.max(np.abs(res["c"] - c_ref) / np.abs(c_ref)))
+    line["c_peak_beta"] = float(betas[int(np.argmax(res["c"]))])
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -299,6 +335,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--serve", action="store_true",
                     help="serving benchmark: Poisson stream of Ising solves through the server")
+    ap.add_argument("--grid", action="store_true",
+                    help="the Ising beta grid (64 betas, D_cut = 32): f, u, c and solves/s")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
     ap.add_argument("--slots", type=int, default=4)
@@ -306,6 +344,8 @@ def main():
     args = ap.parse_args()
     if args.serve:
         return run_serve(args)
+    if args.grid:
+        return run_grid(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
