@@ -303,6 +303,50 @@ def run_grid(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dtrg(args):
+    """Differentiable-TRG MERA updates at the workload's size: start from the
+    HOTRG isometries, then time --steps updates (each a forward with the
+    isometries as parameters, a backward with them fixed, and the SVD update of
+    one steady-state layer) after --warmup untimed ones."""
+    import torch
+    import paper_1912_02780_gb300 as hot
+    d0, d_cut, n, desc = WORKLOADS[args.workload]
+    T0 = synth.random_symmetric_T0(0, d0)
+    kw = dict(split_from_step=args.split_from, hi_precision_steps=args.hi_steps)
+    with hot.Plan(d0, d_cut, n, args.precision, want_grad=True, **kw) as p0:
+        lnz0, _, _ = p0.forward_tensor(T0)
+        ws = p0.isometries()
+    with hot.Plan(d0, d_cut, n, args.precision, want_grad=True, fixed_w_grad=True, w_given=True,
+                  **kw) as p:
+        p.set_isometries(ws)
+        k0 = max(args.split_from + args.hi_steps, 2)    # steady-state layers
+        layers = [k0 + i % (n - k0 + 1) for i in range(args.warmup + args.steps)]
+
+        def update(k):
+            p.forward_tensor(T0)
+            p.backward()
+            p.mera_update(k)
+
+        for k in layers[:args.warmup]:
+            update(k)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for k in layers[args.warmup:]:
+            update(k)
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        lnz1, _, _ = p.forward_tensor(T0)
+    line = {"metric": "dTRG MERA updates/s", "value": args.steps / dt, "unit": "updates/s",
+            "higher_is_better": True, "ms_per_update": 1e3 * dt / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "dtype": args.precision,
+            "data": "synthetic",
+            "config": {"workload": args.workload, "desc": desc, "layers": layers,
+                       "split_from_step": args.split_from, "hi_precision_steps": args.hi_steps,
+                       "update": "forward (isometries given) + backward (w fixed) + SVD of one layer"},
+            "lnz_hotrg": lnz0, "lnz_after_updates": lnz1}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -337,6 +381,8 @@ def main():
                     help="serving benchmark: Poisson stream of Ising solves through the server")
     ap.add_argument("--grid", action="store_true",
                     help="the Ising beta grid (64 betas, D_cut = 32): f, u, c and solves/s")
+    ap.add_argument("--dtrg", action="store_true",
+                    help="time differentiable-TRG MERA updates at the workload's size")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
     ap.add_argument("--slots", type=int, default=4)
@@ -346,6 +392,8 @@ def main():
         return run_serve(args)
     if args.grid:
         return run_grid(args)
+    if args.dtrg:
+        return run_dtrg(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
