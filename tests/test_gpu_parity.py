@@ -124,10 +124,12 @@ def _golden(name):
 
 
 def test_forward_split_c4_d64_against_stored_oracle():
-    """Full-size split-precision solve in the benchmark's configuration
-    (D_cut = 64, 30 steps, FP64 steps 1-4, four bf16 planes on steps 5-6,
-    three after) against the oracle's stored ln Z / N
-    (tests/golden/make_golden.py c4_d64_s0): within the 1e-9 target."""
+    """Full-size split-precision solve (D_cut = 64, 30 steps, FP64 steps 1-4,
+    four bf16 planes on steps 5-6, three after, cuSOLVER's partial
+    eigensolver) against the oracle's stored ln Z / N
+    (tests/golden/make_golden.py c4_d64_s0): within the 1e-9 target.  The
+    benchmark's schedule (split from step 4) is tested with the subspace
+    eigensolver below."""
     g = _golden("c4_d64_s0")
     T0 = synth.random_symmetric_T0(0, 4)
     with hot.Plan(4, 64, 30, "bf16x6", split_from_step=5, want_grad=False,
