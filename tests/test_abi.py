@@ -5,6 +5,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -87,3 +88,11 @@ def test_w_given_needs_fixed_w_gradients(hot):
     assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
     c = hot.make_config(2, 8, 6, w_given=True, fixed_w_grad=True)
     assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 0
+
+
+def test_dtrg_driver_needs_one_input():
+    from paper_1912_02780_gb300.dtrg import dtrg_sweeps
+    with pytest.raises(ValueError):
+        dtrg_sweeps(2, 6, 4, n_sweeps=1)                                  # neither T0 nor beta
+    with pytest.raises(ValueError):
+        dtrg_sweeps(2, 6, 4, n_sweeps=1, T0=np.ones((2, 2, 2, 2)), beta=0.4)   # both
