@@ -110,6 +110,24 @@ typedef struct {
                                with hotrg_set_isometries or left by hotrg_mera_update and
                                forms no Gram and no eigensolve.  Needs want_grad = 1 and
                                fixed_w_grad = 1.                                          */
+  double eigh_residual_tol; /* eigh_mode 1: accuracy guard of the subspace eigensolver.  After
+                               each subspace solve the kept Ritz pairs are checked on the
+                               device, r = max_a ||G v_a - theta_a v_a||_2 / theta_1; a step
+                               with r above this bound (<= 0: 1e-7) is recomputed with the
+                               exact partial eigensolver (cuSOLVER syevdx) together with every
+                               later step, at the next synchronisation (hotrg_sync or the
+                               host-buffer forward).  Must be finite and >= 0.            */
+  int stage2_n_group;       /* tile order of the O(D^7) stage-2 GEMM: its persistent CTAs walk
+                               the output in groups of this many 128-wide N-tiles (all M-tiles
+                               of a group before the next), so that one stripe of the B
+                               operand stays in L2 while A streams; 0 = the default (16);
+                               a value >= the N-tile count = plain N-fastest order.  Results
+                               do not depend on it.                                        */
+  int stage2_prefetch;      /* stage-2 GEMM: its TMA warp prefetches into L2 the K slab this
+                               many 64-wide slabs ahead of the one it loads into shared
+                               memory, so that the load finds its data in L2; 0 = the default
+                               (4), < 0 = no prefetch, at most 64.  Results do not depend on
+                               it.                                                         */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -117,7 +135,8 @@ typedef struct hotrg_plan_s* hotrg_plan;
 /* Fill a config with defaults: FP64, split_from_step = 1, want_grad = 1,
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
- * epilogue_split = 1, split_chunk_elems = 0, w_given = 0.
+ * epilogue_split = 1, split_chunk_elems = 0, w_given = 0, eigh_residual_tol = 0,
+ * stage2_n_group = 0, stage2_prefetch = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
@@ -175,7 +194,10 @@ hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double 
  * are written to the device buffer out_dev = [lnz_per_site, trace_sign,
  * ln c_1 .. ln c_n] (n_steps + 2 doubles).  Enqueued on the plan's stream;
  * returns without synchronising.  Device-side failures (eigensolver,
- * non-finite norm, timeouts) are reported by hotrg_sync. */
+ * non-finite norm, timeouts) are reported by hotrg_sync.  With eigh_mode 1,
+ * out_dev is final only once hotrg_sync has returned: a step that failed the
+ * subspace eigensolver's residual check is recomputed there (see
+ * eigh_residual_tol) and out_dev rewritten. */
 hotrg_status hotrg_forward_device(hotrg_plan plan, const double* T0_dev, double* out_dev);
 
 /* Backward after a forward (needs want_grad = 1).  dlnz_dT0_host: d0^4
@@ -196,6 +218,16 @@ hotrg_status hotrg_sync(hotrg_plan plan);
  * where the step ran in the split tensor-core precision. */
 hotrg_status hotrg_diagnostics(hotrg_plan plan, double* trunc_err, double* cut_gap,
                                int* step_is_split);
+
+/* Eigensolver diagnostics of the last forward (host arrays of n_steps, may be
+ * NULL): residual = the guard's max_a ||G v_a - theta_a v_a||_2 / theta_1 of
+ * the kept Ritz pairs where the subspace eigensolver ran (NaN elsewhere);
+ * exact_step = 1 where the guard fired and the step was recomputed with the
+ * exact partial eigensolver; fallbacks = such recomputations over the plan's
+ * lifetime.  residual holds the last pass's values (the exact recomputation
+ * writes NaN for its step).  Call after hotrg_sync or a host-buffer forward. */
+hotrg_status hotrg_eigh_diagnostics(hotrg_plan plan, double* residual, int* exact_step,
+                                    long long* fallbacks);
 
 /* Per-step bond dimensions of a plan: X (merged legs), Y (other legs), X' (kept). */
 hotrg_status hotrg_step_dims(hotrg_plan plan, int step, int* X, int* Y, int* Xp);
@@ -261,7 +293,8 @@ void hotrg_server_destroy(hotrg_server server);
  * 6 operand preparation (bf16 split), 7 backward contractions, 8 backward
  * eigensolve adjoint, 9 backward Gram adjoint, 10 stage-2 contraction of the
  * four-plane steps; inside slot 1, for the subspace eigensolver: 11 products
- * G Q (with the split of G), 12 QR, 13 Rayleigh-Ritz; slot + 16 = the same
+ * G Q (with the split of G), 12 QR, 13 Rayleigh-Ritz, 14 the residual check of
+ * the kept Ritz pairs; slot + 16 = the same
  * stage run by the FP64 GEMM instead of the tensor-core GEMM. */
 #define HOTRG_PROFILE_SLOTS 32
 hotrg_status hotrg_profile_enable(hotrg_plan plan, int enable);
@@ -304,11 +337,16 @@ hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const do
  * library holds until process exit; sizes with
  * 256 + 2 * planes * (roundup64(M*K) + roundup64(N*K)) > 8 MiB are rejected
  * with HOTRG_EINVAL.  Nothing is allocated: no cudaMalloc, no cudaFree.
- * The first call on a device looks up the array's device address (once per
- * device, with that device current); make that first call before any stream
- * capture.  Work is enqueued on `stream` (a cudaStream_t, NULL = legacy
- * default stream) and the call waits for it.  All calls share the one array,
- * so calls that overlap on the GPU (other threads, other streams) race. */
+ * The operand planes are prepared exactly as hotrg_gemm_split_check prepares
+ * them, so C is the same as that entry point's C.
+ * The first call on a device does a one-time set-up: it looks up the array's
+ * device address and the device's attributes (once per device, with that
+ * device current); make that first call before any stream capture.  Work is
+ * enqueued on `stream` (a cudaStream_t, NULL = legacy default stream); the
+ * call then reads the error word back and synchronises `stream`, so it
+ * returns with C complete.  All calls share the one array and each call
+ * overwrites the previous call's contents, so calls that overlap on the GPU
+ * (other threads, other streams) race. */
 hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes, int kchunk,
                                       const double* A_dev, const double* B_dev, double* C_dev,
                                       void* stream);

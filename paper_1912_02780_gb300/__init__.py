@@ -31,7 +31,7 @@ EXPORTS = (
     "hotrg_isometries", "hotrg_set_isometries", "hotrg_isometry_adjoints", "hotrg_mera_update", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
-    "hotrg_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
+    "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
     "hotrg_gemm_split_noalloc",
@@ -42,7 +42,7 @@ EXPORTS = (
 PROFILE_SLOTS = 32
 STAGE_NAMES = {0: "gram", 1: "eigh", 2: "s1", 3: "s2", 4: "s3", 5: "norm", 6: "prep",
                7: "bwd_contract", 8: "bwd_eigh_adj", 9: "bwd_gram_adj", 10: "s2_4plane",
-               11: "eigh_prod", 12: "eigh_qr", 13: "eigh_rr"}
+               11: "eigh_prod", 12: "eigh_qr", 13: "eigh_rr", 14: "eigh_res"}
 
 
 class hotrg_config(ctypes.Structure):
@@ -53,7 +53,8 @@ class hotrg_config(ctypes.Structure):
                 ("hi_precision_steps", ctypes.c_int), ("eigh_mode", ctypes.c_int),
                 ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int),
                 ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong),
-                ("w_given", ctypes.c_int)]
+                ("w_given", ctypes.c_int), ("eigh_residual_tol", ctypes.c_double),
+                ("stage2_n_group", ctypes.c_int), ("stage2_prefetch", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
     L.hotrg_sync.argtypes = [vp]
     L.hotrg_diagnostics.argtypes = [vp, _dp, _dp, _ip]
     L.hotrg_step_dims.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip]
+    L.hotrg_eigh_diagnostics.argtypes = [vp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong)]
     L.hotrg_status_string.argtypes = [ctypes.c_int]
     L.hotrg_status_string.restype = ctypes.c_char_p
     L.hotrg_last_error.argtypes = [vp]
@@ -162,7 +164,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 hi_precision_steps: int = 2, eigh_mode: int = 0,
                 eigh_power_iters: int = 4, eigh_block: int = 0,
                 epilogue_split: bool = True, split_chunk_elems: int = 0,
-                w_given: bool = False) -> hotrg_config:
+                w_given: bool = False, eigh_residual_tol: float = 0.0,
+                stage2_n_group: int = 0, stage2_prefetch: int = 0) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -178,6 +181,9 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.epilogue_split = int(bool(epilogue_split))
     c.split_chunk_elems = int(split_chunk_elems)
     c.w_given = int(bool(w_given))
+    c.eigh_residual_tol = float(eigh_residual_tol)
+    c.stage2_n_group = int(stage2_n_group)
+    c.stage2_prefetch = int(stage2_prefetch)
     return c
 
 
@@ -204,11 +210,13 @@ class Plan:
                  gram_split_from_step: int = 0, hi_precision_steps: int = 2,
                  eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0,
                  epilogue_split: bool = True, split_chunk_elems: int = 0,
-                 w_given: bool = False):
+                 w_given: bool = False, eigh_residual_tol: float = 0.0,
+                 stage2_n_group: int = 0, stage2_prefetch: int = 0):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
-                               epilogue_split, split_chunk_elems, w_given)
+                               epilogue_split, split_chunk_elems, w_given, eigh_residual_tol,
+                               stage2_n_group, stage2_prefetch)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))
@@ -263,6 +271,17 @@ class Plan:
         s = np.zeros(self.n_steps, dtype=np.int32)
         self._check(lib().hotrg_diagnostics(self._h, _p(t), _p(g), s.ctypes.data_as(_ip)), "diagnostics")
         return t, g, s
+
+    def eigh_diagnostics(self):
+        """(residual per step, exact-fallback flag per step, fallbacks so far):
+        the subspace eigensolver's accuracy guard (NaN residual where it did
+        not run)."""
+        r = np.zeros(self.n_steps)
+        e = np.zeros(self.n_steps, dtype=np.int32)
+        f = ctypes.c_longlong(0)
+        self._check(lib().hotrg_eigh_diagnostics(self._h, _p(r), e.ctypes.data_as(_ip),
+                                                 ctypes.byref(f)), "eigh_diagnostics")
+        return r, e, int(f.value)
 
     # ---- differentiable TRG: isometries as parameters ----------------------
     def _w_layout(self):

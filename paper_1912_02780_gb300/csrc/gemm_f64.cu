@@ -9,7 +9,9 @@
 // device (about 2 DFMA per clock per SM on GB300), not by memory, so the
 // kernel keeps one 64x64 tile per 256-thread block with 4x4 outputs per
 // thread and a 16-deep K slab in shared memory.  Very long K with a small
-// output grid is split across blocks (split-K) and reduced with atomics.
+// output grid is split across blocks (split-K) when the caller provides a
+// workspace for the partials, which are then summed in a fixed order, so the
+// result never depends on the order in which blocks finish.
 #include "common.cuh"
 #include "gemm_f64.h"
 
@@ -97,10 +99,8 @@ __global__ void __launch_bounds__(256) gemm_f64_kernel(GemmF64 p, int k_per_spli
       }
       double* c = p.C + off;
       double v = p.alpha * acc[i][j];
-      if (gridDim.z > 1 && p.ws) {
+      if (gridDim.z > 1) {
         p.ws[((long long)blockIdx.z * p.M + m) * p.N + n] = acc[i][j];
-      } else if (gridDim.z > 1) {
-        atomicAdd(c, v);
       } else {
         *c = (p.beta != 0.0) ? v + p.beta * *c : v;
       }
@@ -162,14 +162,17 @@ cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms) {
     k_per_split = ((p.K + splits - 1) / splits + BK - 1) / BK * BK;
     splits = (p.K + k_per_split - 1) / k_per_split;
   }
-  const bool det = splits > 1 && p.ws && (long long)splits * p.M * p.N <= p.ws_elems;
-  if (splits > 1 && !det) {
-    long long total = (long long)p.M * p.N;
-    int blocks = (int)((total + 255) / 256);
-    if (blocks > 8 * num_sms) blocks = 8 * num_sms;
-    count_launch();
-    scale_out_kernel<<<blocks, 256, 0, stream>>>(p);
+  if (splits > 1) {
+    // as many splits as the workspace holds partials for (none: no split-K)
+    const long long mn = (long long)p.M * p.N;
+    const long long fit = p.ws ? p.ws_elems / mn : 0;
+    if (fit < splits) {
+      splits = fit >= 2 ? (int)fit : 1;
+      k_per_split = splits > 1 ? ((p.K + splits - 1) / splits + BK - 1) / BK * BK : p.K;
+      if (splits > 1) splits = (p.K + k_per_split - 1) / k_per_split;
+    }
   }
+  const bool det = splits > 1;
   if (splits > 1) grid.z = splits;
   if (p.K <= 0) {
     if (splits == 1) {
@@ -183,7 +186,6 @@ cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms) {
     return cudaGetLastError();
   }
   GemmF64 q = p;
-  if (!det) q.ws = nullptr;
   count_launch();
   gemm_f64_kernel<<<grid, 256, 0, stream>>>(q, k_per_split);
   if (det) {

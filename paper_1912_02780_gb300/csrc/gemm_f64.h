@@ -14,8 +14,9 @@ struct GemmF64 {
   long long a_lim, b_lim, c_lim;  // element counts behind A, B, C: accesses at or beyond
                                   // them are skipped and flagged (kErrBounds)
   int* err;
-  double* ws;                     // optional split-K workspace: with it, split-K partials are
-  long long ws_elems;             // summed in a fixed order (deterministic); without, atomics
+  double* ws;                     // optional split-K workspace: split-K partials are summed in
+  long long ws_elems;             // a fixed order; splits are limited to what it holds (none:
+                                  // no split-K), so the result is always deterministic
 };
 
 cudaError_t gemm_f64(const GemmF64& p, cudaStream_t stream, int num_sms);

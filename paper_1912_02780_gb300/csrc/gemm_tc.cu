@@ -93,6 +93,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
+// L2 prefetch of one tensor-map box (no shared memory, no completion).
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* tm, int c0, int c1, int c2) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                   (uint64_t)tm),
+               "r"(c0), "r"(c1), "r"(c2)
+               : "memory");
+}
+
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -224,12 +232,24 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Tile t of an MT x NT grid: M fastest (m_fast) or N fastest.
-__device__ __forceinline__ void tile_coords(long long t, int MT, int NT, int m_fast, int& mt,
-                                            int& nt) {
+// Tile t of an MT x NT grid: M fastest (m_fast), N fastest, or (n_group > 0)
+// in groups of n_group N-tiles: all M-tiles of one group of columns, N fastest
+// inside the group, before the next group.  The persistent CTAs then work on
+// one stripe of B at a time, which stays in L2 while A streams past it; A is
+// read once per group.
+__device__ __forceinline__ void tile_coords(long long t, int MT, int NT, int m_fast, int n_group,
+                                            int& mt, int& nt) {
   if (m_fast) {
     nt = (int)(t / MT);
     mt = (int)(t - (long long)nt * MT);
+  } else if (n_group > 0 && n_group < NT) {
+    const long long per_group = (long long)MT * n_group;
+    const int grp = (int)(t / per_group);
+    const long long r = t - (long long)grp * per_group;
+    const int n0 = grp * n_group;
+    const int gw = (NT - n0) < n_group ? (NT - n0) : n_group;   // the last group may be narrower
+    mt = (int)(r / gw);
+    nt = n0 + (int)(r - (long long)mt * gw);
   } else {
     mt = (int)(t / NT);
     nt = (int)(t - (long long)mt * NT);
@@ -420,10 +440,33 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
       int issued[C::kStages];
       uint32_t last_par[C::kStages];
       for (int i = 0; i < C::kStages; ++i) { issued[i] = 0; last_par[i] = 0; }
+      const int pf = p.prefetch;
       for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
         int mt, nt;
-        tile_coords(t, MT, NT, p.m_fast, mt, nt);
+        tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
+        int pmt = -1, pnt = -1;   // the CTA's next tile, for prefetches past this one's end
+        if (pf > 0 && t + gridDim.x < tiles)
+          tile_coords(t + gridDim.x, MT, NT, p.m_fast, p.n_group, pmt, pnt);
+        if (pf > 0 && t == blockIdx.x) {
+          // the first slabs of the first tile
+          for (int q = 0; q < pf && q < KB; ++q) {
+            for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, q * BK, mt * BM, pl);
+            for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, q * BK, nt * BN, pl);
+          }
+        }
         for (int kb = 0; kb < KB; ++kb) {
+          if (pf > 0) {
+            // warm L2 with the slab `pf` ahead (of this tile, else of the next
+            // one), so that the TMA load of it finds its data there
+            const int q = kb + pf;
+            if (q < KB) {
+              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, q * BK, mt * BM, pl);
+              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, q * BK, nt * BN, pl);
+            } else if (pmt >= 0 && q - KB < KB) {
+              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, (q - KB) * BK, pmt * BM, pl);
+              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, (q - KB) * BK, pnt * BN, pl);
+            }
+          }
           if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err)) { ok = false; break; }
           mbar_expect_tx(full_bar(s), C::kStage);
 #pragma unroll
@@ -499,7 +542,7 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
     float rhi[C::kCols], rlo[C::kCols];
     for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
       int mt, nt;
-      tile_coords(t, MT, NT, p.m_fast, mt, nt);
+      tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
       const int m0 = mt * BM, n0 = nt * BN;
       const int m = m0 + row;
       const bool mok = m < p.M;

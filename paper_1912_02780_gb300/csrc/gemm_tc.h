@@ -42,6 +42,10 @@ struct TcGemm {
                              // planes, 32 for four)
   int m_fast;                // tile order: 1 = consecutive tiles walk M (B tile reused from
                              // L2 by neighbouring CTAs), 0 = consecutive tiles walk N
+  int n_group;               // with m_fast = 0 and n_group > 0: tiles in groups of n_group
+                             // N-tiles (an L2-resident stripe of B), M-major inside
+  int prefetch;              // > 0: the TMA warp prefetches into L2 the K slab this many
+                             // slabs ahead of the one it loads (0: no prefetch)
   int seg_prow, seg_phalf;   // kOutGridSplit: segment partner of (row, half)
 };
 

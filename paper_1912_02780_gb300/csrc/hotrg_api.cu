@@ -151,7 +151,13 @@ struct hotrg_plan_s {
   double *Ecur = nullptr, *Enext = nullptr, *Tbar = nullptr;
   double *dT0 = nullptr, *partial = nullptr, *scal = nullptr, *log_norms = nullptr, *out = nullptr;
   double *dtrunc = nullptr, *dgap = nullptr;
-  int* err = nullptr;
+  double* dres = nullptr;     // per step: max relative residual of the kept Ritz pairs
+  int* err = nullptr;         // [0] all error bits, [1] first bit, [2] residual guard code
+  // subspace eigensolver guard: steps of the current forward recomputed with
+  // the exact partial eigensolver, and the count of such recomputations
+  std::vector<char> exact_step;
+  long long fallbacks = 0;
+  double* pending_out = nullptr;   // device out buffer of the last hotrg_forward_device
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
@@ -262,6 +268,8 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->eigh_mode < 0 || c->eigh_mode > 1) return HOTRG_EINVAL;
   if (c->split_chunk_elems < 0 || c->split_chunk_elems > (1LL << 34)) return HOTRG_EINVAL;
   if (c->w_given && (!c->want_grad || !c->fixed_w_grad)) return HOTRG_EINVAL;
+  if (!std::isfinite(c->eigh_residual_tol) || c->eigh_residual_tol < 0) return HOTRG_EINVAL;
+  if (c->stage2_n_group < 0 || c->stage2_prefetch > 64) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -337,7 +345,8 @@ TcOperand opnd(const __nv_bfloat16* ptr, int rows, int K, int planes, long long 
 
 enum StageId { kStGram = 0, kStEigh = 1, kStS1 = 2, kStS2 = 3, kStS3 = 4, kStNorm = 5,
                kStPrep = 6, kStBwdContract = 7, kStBwdEigh = 8, kStBwdGram = 9, kStS2Hi = 10,
-               kStEighProd = 11, kStEighQR = 12, kStEighRR = 13, kStF64 = 16 };
+               kStEighProd = 11, kStEighQR = 12, kStEighRR = 13, kStEighRes = 14,
+               kStF64 = 16 };
 
 hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* A, double* B,
                       double* G) {
@@ -419,6 +428,15 @@ hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, cons
   return HOTRG_OK;
 }
 
+// N-tiles per L2 raster group of the stage-2 GEMM (0 in the config: the
+// default; >= the N-tile count: plain N-fastest order).
+int stage2_group(const hotrg_config& c) { return c.stage2_n_group > 0 ? c.stage2_n_group : 16; }
+// K slabs between the stage-2 GEMM's L2 prefetch and its TMA load (config:
+// 0 = the default, < 0 = no prefetch).
+int stage2_prefetch(const hotrg_config& c) {
+  return c.stage2_prefetch > 0 ? c.stage2_prefetch : (c.stage2_prefetch < 0 ? 0 : 4);
+}
+
 // Segment partner of the grid-split epilogue (see gemm_tc.h: kOutGridSplit)
 // for an output whose 64-column half-runs are `run` consecutive destination
 // elements of the consumer's K: the other half of a 128-segment is in the
@@ -484,6 +502,8 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
                     fuse2 ? (void*)p->pV : stage_buf(p, np), fuse2 ? sC : 0);
     g2.seg_prow = p2r;
     g2.seg_phalf = p2h;
+    g2.n_group = stage2_group(p->cfg);
+    g2.prefetch = stage2_prefetch(p->cfg);
     CK(tc_gemm(u, pp, g2, st, p->sms));
     }
     if (!fuse2) {
@@ -532,6 +552,12 @@ int subspace_ritz(const StepGeom& s) { return s.Xp + 1; }
 // D' + 1 leading Ritz vectors (ascending Ritz values) in p->Zs as contiguous
 // rows and their Ritz values in p->wasc, ready for eig_desc.
 constexpr int kEighPlanes = 4;
+
+// Residual bound of the kept Ritz pairs, relative to the largest eigenvalue,
+// above which a step's subspace eigensolve is replaced by the exact one.
+double residual_tol(const hotrg_config& c) {
+  return c.eigh_residual_tol > 0 ? c.eigh_residual_tol : 1e-7;
+}
 
 bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
   if (!s.split || !p->pU || !p->pV) return false;
@@ -612,6 +638,36 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
   return HOTRG_OK;
 }
 
+// Accuracy guard of the subspace eigensolver: the kept Ritz pairs (rows of
+// Ek, values lk descending) are checked against the Gram matrix still in
+// p->Escr, r = max_a ||G v_a - theta_a v_a|| / theta_1.  On split steps the
+// products run on the four-plane tensor-core GEMM with the split of G the
+// eigensolver made; otherwise in FP64.  A step over the bound raises the
+// guard word err[2] to n + 1 - k (the earliest failing step wins); the host
+// sees it at the next synchronisation and recomputes the forward from that
+// step with the exact partial eigensolver (finish_sync), so the good path
+// costs one product per step and no host synchronisation.
+hotrg_status eigh_residual(hotrg_plan p, const StepGeom& s, int k) {
+  Stage sc(p, kStEighRes);
+  cudaStream_t st = p->stream;
+  const int N = (int)s.N, Dp = s.Xp;
+  const double* Ek = E_of(p, k);
+  if (subspace_on_tc(p, s)) {
+    const long long sE = round_up((long long)Dp * N, 64), sG = round_up((long long)N * N, 64);
+    CK(gsplit(p, Ek, map_lin(N), map_lin(1), Dp, N, kEighPlanes, sE, p->pU));
+    CK(tc_gemm(opnd(p->pU, Dp, N, kEighPlanes, sE), opnd(p->pV, N, N, kEighPlanes, sG),
+               tcg(p, kEighPlanes, Dp, N, N, map_lin(N), map_lin(1), kOutF64, p->Zs, 0), st,
+               p->sms));
+  } else {
+    CK(gemm_f64(g64(p, Ek, map_lin(N), map_lin(1), p->Escr, map_lin(N), map_lin(1), p->Zs,
+                    map_lin(N), map_lin(1), Dp, N, N, 1.0, 0.0),
+                st, p->sms));
+  }
+  CK(eig_residual(p->Zs, Ek, p->lam[k - 1], Dp, N, residual_tol(p->cfg), p->partial,
+                  p->dres + (k - 1), p->err + 2, p->cfg.n_steps + 1 - k, st));
+  return HOTRG_OK;
+}
+
 hotrg_status step_forward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
   cudaStream_t st = p->stream;
@@ -635,7 +691,9 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   CK(diag_trace(p->Escr, N, p->scal + 3, st));
   int ncols = N;
   const double* evec = p->Escr;
-  if (use_subspace(p, s)) {
+  const bool exact = (size_t)(k - 1) < p->exact_step.size() && p->exact_step[k - 1];
+  const bool subspace = use_subspace(p, s) && !exact;
+  if (subspace) {
     hotrg_status rr = eigh_subspace(p, s, k);
     if (rr != HOTRG_OK) return rr;
     ncols = subspace_ritz(s);
@@ -661,6 +719,12 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     CK(set_value(nullptr, 0.0, p->err, kErrEigh, st));
   CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
   CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
+  if (subspace) {
+    hotrg_status rr = eigh_residual(p, s, k);
+    if (rr != HOTRG_OK) return rr;
+  } else {
+    CK(set_value(p->dres + (k - 1), std::nan(""), nullptr, 0, st));
+  }
   }
   }
   if (s.split) r = contract_split(p, s, T, Ek, Tout);
@@ -675,12 +739,12 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   return HOTRG_OK;
 }
 
-hotrg_status run_forward(hotrg_plan p) {
+hotrg_status run_forward(hotrg_plan p, int k_from = 1) {
   cudaStream_t st = p->stream;
   if (p->cfg.w_given && !p->w_loaded)
     return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
   p->have_bwd = false;
-  for (int k = 1; k <= p->cfg.n_steps; ++k) {
+  for (int k = k_from; k <= p->cfg.n_steps; ++k) {
     hotrg_status r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
   }
@@ -854,9 +918,7 @@ hotrg_status run_backward(hotrg_plan p) {
   return HOTRG_OK;
 }
 
-hotrg_status check_device_error(hotrg_plan p) {
-  int w[2] = {0, 0};
-  CK(cudaMemcpy(w, p->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+hotrg_status device_status(hotrg_plan p, const int* w) {
   // the first failure recorded is the root cause; report it first
   const int e = w[1] ? w[1] : w[0];
   if (e & kErrTimeout) return fail(p, HOTRG_ETIMEOUT, "device wait timed out");
@@ -867,9 +929,31 @@ hotrg_status check_device_error(hotrg_plan p) {
   return HOTRG_OK;
 }
 
+// Wait for the plan's stream and turn the device error word into a status.
+// When the residual guard of the subspace eigensolver fired during a forward,
+// recompute that forward from the earliest failing step with the exact
+// partial eigensolver at that step (later steps keep the subspace solver and
+// their own checks), then wait again.  Each pass moves the restart point
+// forward, so this ends after at most n_steps passes.
 hotrg_status finish_sync(hotrg_plan p) {
-  CK(cudaStreamSynchronize(p->stream));
-  return check_device_error(p);
+  for (;;) {
+    CK(cudaStreamSynchronize(p->stream));
+    int w[3] = {0, 0, 0};
+    CK(cudaMemcpy(w, p->err, 3 * sizeof(int), cudaMemcpyDeviceToHost));
+    hotrg_status r = device_status(p, w);
+    if (r != HOTRG_OK || w[2] == 0) return r;
+    const int n = p->cfg.n_steps, k = n + 1 - w[2];
+    if (k < 1 || k > n || (int)p->exact_step.size() != n || p->exact_step[k - 1])
+      return fail(p, HOTRG_ENOTCONV, "subspace eigensolver guard: bad restart step");
+    p->exact_step[k - 1] = 1;
+    ++p->fallbacks;
+    CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), p->stream));
+    r = run_forward(p, k);
+    if (r != HOTRG_OK) return r;
+    if (p->pending_out)
+      CK(cudaMemcpyAsync(p->pending_out, p->out, sizeof(double) * (n + 2),
+                         cudaMemcpyDeviceToDevice, p->stream));
+  }
 }
 
 }  // namespace
@@ -969,6 +1053,9 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->epilogue_split = 1;
   c->split_chunk_elems = 0;
   c->w_given = 0;
+  c->eigh_residual_tol = 0.0;
+  c->stage2_n_group = 0;
+  c->stage2_prefetch = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -1094,6 +1181,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   ALC(p->out, n + 2);
   ALC(p->dtrunc, n);
   ALC(p->dgap, n);
+  ALC(p->dres, n);
   ALC(p->err, 4);
   ALC(p->info, 4);
   if (L.any_split) {
@@ -1177,7 +1265,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       ALC(p->swork, (long long)ls);
     }
   }
-  if (cudaMemset(p->err, 0, 2 * sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
+  if (cudaMemset(p->err, 0, 3 * sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
 #undef ALC
   *out = p;
   return HOTRG_OK;
@@ -1198,7 +1286,9 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
   if (!p || !T0_dev) return fail(p, HOTRG_EINVAL, "null argument");
   const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
   p->have_fwd = false;
-  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), p->stream));
+  p->exact_step.assign(p->cfg.n_steps, 0);
+  p->pending_out = out_dev;
+  CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), p->stream));
   if (T0_dev != p->T[0])
     CK(cudaMemcpyAsync(p->T[0], T0_dev, sizeof(double) * n0, cudaMemcpyDeviceToDevice, p->stream));
   hotrg_status r = run_forward(p);
@@ -1213,13 +1303,16 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
 
 static hotrg_status copy_out(hotrg_plan p, double* lnz, double* log_norms, int* sign) {
   std::vector<double> h(p->cfg.n_steps + 2);
-  CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
-                     p->stream));
+  // the forward is final only after finish_sync (which may recompute steps
+  // whose subspace eigensolve failed its residual check)
   hotrg_status r = finish_sync(p);
   if (r != HOTRG_OK) {
     p->have_fwd = false;
     return r;
   }
+  CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                     p->stream));
+  CK(cudaStreamSynchronize(p->stream));
   if (lnz) *lnz = h[0];
   if (sign) *sign = h[1] >= 0 ? 1 : -1;
   if (log_norms) memcpy(log_norms, h.data() + 2, sizeof(double) * p->cfg.n_steps);
@@ -1256,7 +1349,7 @@ hotrg_status hotrg_backward_device(hotrg_plan p, double* grad_dev) {
   if (!p) return HOTRG_EINVAL;
   if (!p->cfg.want_grad) return fail(p, HOTRG_ESTATE, "plan created with want_grad = 0");
   if (!p->have_fwd) return fail(p, HOTRG_ESTATE, "backward needs a forward first");
-  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), p->stream));
+  CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), p->stream));
   hotrg_status r = run_backward(p);
   if (r != HOTRG_OK) return r;
   p->have_bwd = true;
@@ -1298,6 +1391,18 @@ hotrg_status hotrg_diagnostics(hotrg_plan p, double* trunc, double* gap, int* is
   if (gap) CK(cudaMemcpy(gap, p->dgap, sizeof(double) * n, cudaMemcpyDeviceToHost));
   if (is_split)
     for (int k = 0; k < n; ++k) is_split[k] = p->L.g[k].split ? 1 : 0;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_eigh_diagnostics(hotrg_plan p, double* residual, int* exact_step,
+                                    long long* fallbacks) {
+  if (!p) return HOTRG_EINVAL;
+  const int n = p->cfg.n_steps;
+  if (residual) CK(cudaMemcpy(residual, p->dres, sizeof(double) * n, cudaMemcpyDeviceToHost));
+  if (exact_step)
+    for (int k = 0; k < n; ++k)
+      exact_step[k] = (int)p->exact_step.size() == n ? p->exact_step[k] : 0;
+  if (fallbacks) *fallbacks = p->fallbacks;
   return HOTRG_OK;
 }
 
@@ -1357,7 +1462,7 @@ hotrg_status hotrg_mera_update(hotrg_plan p, int k) {
   const StepGeom& g = p->L.g[k - 1];
   const int N = (int)g.N, Xp = g.Xp;
   cudaStream_t st = p->stream;
-  CK(cudaMemsetAsync(p->err, 0, 2 * sizeof(int), st));
+  CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), st));
   // E_w (rows = kept vectors) is the N x Xp column-major matrix cuSOLVER reads
   CK(cudaMemcpyAsync(p->Gb, p->wbar_all + p->w_off[k - 1], sizeof(double) * (size_t)Xp * N,
                      cudaMemcpyDeviceToDevice, st));

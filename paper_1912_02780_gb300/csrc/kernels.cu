@@ -408,6 +408,47 @@ __global__ void eig_diag_kernel(const double* __restrict__ lam, int nlam, int N,
   }
 }
 
+// Residual check of the kept Ritz pairs of the subspace eigensolver.
+// Rows a < Dp of V hold the sign-fixed Ritz vectors (descending Ritz values
+// lam), rows of Z = V G the products with the Gram matrix; the first kernel
+// writes r_a = ||Z_a - lam_a V_a||_2 for each row (one block per row, fixed
+// reduction order), the second max_a r_a / lam_0 to *res and raises *guard to
+// `code` when that exceeds tol (or is not a number).
+__global__ void eig_residual_rows_kernel(const double* __restrict__ Z,
+                                         const double* __restrict__ V,
+                                         const double* __restrict__ lam, int N,
+                                         double* __restrict__ r) {
+  const int a = blockIdx.x;
+  const double la = lam[a];
+  const double* z = Z + (long long)a * N;
+  const double* v = V + (long long)a * N;
+  double acc = 0.0;
+  for (int i = threadIdx.x; i < N; i += blockDim.x) {
+    const double d = z[i] - la * v[i];
+    acc += d * d;
+  }
+  __shared__ double s[256];
+  s[threadIdx.x] = acc;
+  __syncthreads();
+  for (int o = blockDim.x / 2; o > 0; o >>= 1) {
+    if (threadIdx.x < o) s[threadIdx.x] += s[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) r[a] = sqrt(s[0]);
+}
+
+__global__ void eig_residual_max_kernel(const double* __restrict__ r, int Dp,
+                                        const double* __restrict__ lam, double tol, double* res,
+                                        int* guard, int code) {
+  if (threadIdx.x != 0) return;
+  double worst = 0.0;
+  for (int a = 0; a < Dp; ++a) worst = fmax(worst, r[a]);
+  const double l0 = lam[0];
+  const double q = l0 > 0.0 ? worst / l0 : (worst > 0.0 ? INFINITY : 0.0);
+  *res = q;
+  if (!(q <= tol)) atomicMax(guard, code);
+}
+
 __global__ void eigh_info_kernel(const int* info, int* err) {
   if (threadIdx.x == 0 && *info != 0) report_error(err, kErrEigh);
 }
@@ -602,6 +643,16 @@ cudaError_t eig_diag(const double* lam, int nlam, int N, int Dp, const double* t
                      double* gap, cudaStream_t st) {
   count_launch();
   eig_diag_kernel<<<1, 256, 0, st>>>(lam, nlam, N, Dp, trace, trunc, gap);
+  return cudaGetLastError();
+}
+
+cudaError_t eig_residual(const double* Z, const double* V, const double* lam, int Dp, int N,
+                         double tol, double* row_scratch, double* res, int* guard, int code,
+                         cudaStream_t st) {
+  count_launch();
+  eig_residual_rows_kernel<<<Dp, 256, 0, st>>>(Z, V, lam, N, row_scratch);
+  count_launch();
+  eig_residual_max_kernel<<<1, 32, 0, st>>>(row_scratch, Dp, lam, tol, res, guard, code);
   return cudaGetLastError();
 }
 

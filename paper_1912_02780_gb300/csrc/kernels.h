@@ -30,6 +30,12 @@ cudaError_t eig_desc(const double* asc, const double* w_asc, int N, int ncols, i
 cudaError_t diag_trace(const double* G, int N, double* out, cudaStream_t st);
 cudaError_t eig_diag(const double* lam, int nlam, int N, int Dp, const double* trace, double* trunc,
                      double* gap, cudaStream_t st);
+// Kept Ritz pairs (rows of V, values lam descending) against Z = V G:
+// *res = max_{a < Dp} ||Z_a - lam_a V_a||_2 / lam_0; *guard = max(*guard, code)
+// when *res > tol.  row_scratch holds Dp doubles.
+cudaError_t eig_residual(const double* Z, const double* V, const double* lam, int Dp, int N,
+                         double tol, double* row_scratch, double* res, int* guard, int code,
+                         cudaStream_t st);
 cudaError_t eigh_info_check(const int* info, int* err, cudaStream_t st);
 cudaError_t seed_trace_adjoint(double* E, int P, int Q, const double* tr, cudaStream_t st, int sms);
 cudaError_t eigh_adj_scale(double* S, int nd, int Dp, const double* lam, double eta_rel,

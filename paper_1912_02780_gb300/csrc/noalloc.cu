@@ -26,61 +26,64 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
-unsigned char* g_ptr[kMaxDevices] = {};
+struct DeviceInfo {
+  unsigned char* scratch = nullptr;   // device address of g_noalloc_scratch
+  int sms = 0;                        // multiprocessor count
+  bool supported = false;             // compute capability 10.3
+};
+DeviceInfo g_dev[kMaxDevices];
 
 long long round_up64(long long v) { return (v + 63) / 64 * 64; }
 
-// Device address of the scratch array on the current device.  The array's
-// name in host code is only a host-side stand-in, so the address is looked up
-// once per device (with that device current) and cached.
-hotrg_status scratch_on_current_device(unsigned char** out) {
+// Set-up of the current device, done once and cached: the device address of
+// the scratch array (its name in host code is only a host-side stand-in, so
+// the address is looked up with the device current) and the two attributes
+// the launch needs.
+hotrg_status device_info(DeviceInfo* out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return HOTRG_ECUDA;
   std::lock_guard<std::mutex> lk(g_mu);
-  if (!g_ptr[dev]) {
+  DeviceInfo& d = g_dev[dev];
+  if (!d.scratch) {
     void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) {
-      cudaGetLastError();
+    int major = 0, minor = 0, sms = 0;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p ||
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        sms <= 0)
       return HOTRG_ECUDA;
-    }
-    g_ptr[dev] = static_cast<unsigned char*>(p);
+    d.sms = sms;
+    d.supported = major == 10 && minor == 3;
+    d.scratch = static_cast<unsigned char*>(p);
   }
-  *out = g_ptr[dev];
+  *out = d;
   return HOTRG_OK;
 }
 
-}  // namespace
-
-extern "C" hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes, int kchunk,
-                                                 const double* A_dev, const double* B_dev,
-                                                 double* C_dev, void* stream) {
+hotrg_status run(int M, int N, int K, int planes, int kchunk, const double* A_dev,
+                 const double* B_dev, double* C_dev, cudaStream_t s) {
   using namespace hotrg;
-  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || (planes != 2 && planes != 3) || !A_dev ||
-      !B_dev || !C_dev)
-    return HOTRG_EINVAL;
   const long long sa = round_up64((long long)M * K), sb = round_up64((long long)N * K);
   const long long need = (long long)kHeader + 2LL * planes * (sa + sb);
   if (need > (long long)kScratchBytes) return HOTRG_EINVAL;   // operands exceed the scratch
-  unsigned char* base = nullptr;
-  hotrg_status st = scratch_on_current_device(&base);
+  DeviceInfo d;
+  hotrg_status st = device_info(&d);
   if (st != HOTRG_OK) return st;
-  int dev = 0;
-  cudaDeviceProp prop;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaGetDeviceProperties(&prop, dev) != cudaSuccess)
-    return HOTRG_ECUDA;
-  if (!(prop.major == 10 && prop.minor == 3)) return HOTRG_EUNSUPPORTED;
-  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
-  int* err = reinterpret_cast<int*>(base);
-  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(base + kHeader);
+  if (!d.supported) return HOTRG_EUNSUPPORTED;
+  int* err = reinterpret_cast<int*>(d.scratch);
+  __nv_bfloat16* pa = reinterpret_cast<__nv_bfloat16*>(d.scratch + kHeader);
   __nv_bfloat16* pb = pa + (size_t)planes * sa;
-  const int sms = prop.multiProcessorCount;
   // The scratch keeps the previous call's contents: the error words (all bits
   // seen, first bit seen) must start at zero.
   if (cudaMemsetAsync(err, 0, 2 * sizeof(int), s) != cudaSuccess) return HOTRG_ECUDA;
-  if (gather_split(A_dev, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, s,
-                   sms) != cudaSuccess ||
-      gather_split(B_dev, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, s,
-                   sms) != cudaSuccess)
+  // Operand planes exactly as hotrg_gemm_split_check prepares them: plane 0
+  // on the per-segment power-of-two grid that the exact hi*hi accumulation
+  // of the GEMM relies on.
+  if (grid_split(A_dev, (long long)M * K, map_lin(K), map_lin(1), M, K, planes, sa, pa, err, s,
+                 d.sms) != cudaSuccess ||
+      grid_split(B_dev, (long long)N * K, map_lin(K), map_lin(1), N, K, planes, sb, pb, err, s,
+                 d.sms) != cudaSuccess)
     return HOTRG_ECUDA;
   TcGemm g;
   memset(&g, 0, sizeof(g));
@@ -92,7 +95,7 @@ extern "C" hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes
   TcOperand a, b;
   a.ptr = pa; a.rows = M; a.K = K; a.planes = planes; a.plane_stride = sa;
   b.ptr = pb; b.rows = N; b.K = K; b.planes = planes; b.plane_stride = sb;
-  if (tc_gemm(a, b, g, s, sms) != cudaSuccess) return HOTRG_ECUDA;
+  if (tc_gemm(a, b, g, s, d.sms) != cudaSuccess) return HOTRG_ECUDA;
   int e = 0;
   if (cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
       cudaStreamSynchronize(s) != cudaSuccess)
@@ -100,4 +103,20 @@ extern "C" hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes
   if (e & kErrTimeout) return HOTRG_ETIMEOUT;
   if (e) return HOTRG_ECUDA;
   return HOTRG_OK;
+}
+
+}  // namespace
+
+extern "C" hotrg_status hotrg_gemm_split_noalloc(int M, int N, int K, int planes, int kchunk,
+                                                 const double* A_dev, const double* B_dev,
+                                                 double* C_dev, void* stream) {
+  if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || (planes != 2 && planes != 3) || !A_dev ||
+      !B_dev || !C_dev)
+    return HOTRG_EINVAL;
+  const hotrg_status st =
+      run(M, N, K, planes, kchunk, A_dev, B_dev, C_dev, reinterpret_cast<cudaStream_t>(stream));
+  // A failed CUDA call leaves the runtime's last-error state set; clear it so
+  // that a later, unrelated call of the caller does not report it.
+  if (st != HOTRG_OK) cudaGetLastError();
+  return st;
 }

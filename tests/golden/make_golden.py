@@ -11,6 +11,10 @@ Cases:
   c4_d64_s1   same, seed 1
   c3_bc_h0    Ising at beta_c, h = 0, D_cut = 64, 40 steps (forward)
   c3_bc_h001  Ising at beta_c, h = 0.01, D_cut = 64, 40 steps (forward)
+  c3_bc_h0_grad, c3_bc_h001_grad
+              the same two Ising cases with the full backward: d(ln Z/N)/d T0 (16
+              entries, per site, w(T) differentiated) and d(ln Z/N)/d beta
+  c1_ising    Ising at beta = 0.44, h = 0, D_cut = 8, 20 steps (forward + full backward)
   c2_grid     Ising, 64 betas on [0.30, 0.60], D_cut = 32, 30 steps (forward + d/dbeta)
   c4_d96_s0_n7  random T0 (d0 = 4, seed 0), D_cut = 96, 7 steps (forward; steps 5-7 at the
               full D_cut = 96 bond dimensions)
@@ -41,6 +45,26 @@ def fwd_case(name, T0, d_cut, n, meta):
     print(name, out["lnz"], f"{out['oracle_seconds']:.1f}s", flush=True)
 
 
+def grad_case(name, beta, J, h, d_cut, n):
+    """Forward with checkpoints, then the oracle's reverse-mode backward
+    (SM Sec. B recursion, SM Sec. E chain rule, eigensolve adjoint)."""
+    t = time.time()
+    T0 = ising.ising_T0(beta, J, h)
+    f = hotrg.hotrg_forward(T0, d_cut, n, keep=True)
+    t_fwd = time.time() - t
+    g = hotrg.hotrg_backward(f)
+    db = float(np.sum(g * ising.ising_dT0_dbeta(beta, J, h)))
+    out = dict(model="ising", beta=beta, J=J, h=h, d0=2, d_cut=d_cut, n_steps=n,
+               lnz=f["lnz"], log_norms=f["log_norms"], trace_sign=f["trace_sign"],
+               trunc_err=f["trunc_err"],
+               cut_gap=[x if np.isfinite(x) else None for x in f["cut_gap"]],
+               dlnz_dT0=[float(v) for v in g.ravel()], dlnz_dbeta=db,
+               euler=float(np.sum(g * T0)), eta_rel=hotrg.ETA_REL_DEFAULT,
+               oracle_seconds_forward=t_fwd, oracle_seconds=time.time() - t)
+    json.dump(out, open(os.path.join(HERE, name + ".json"), "w"), indent=1)
+    print(name, out["lnz"], db, out["euler"], f"{out['oracle_seconds']:.1f}s", flush=True)
+
+
 def main(cases):
     for c in cases:
         if c.startswith("c4_d64_s"):
@@ -56,6 +80,12 @@ def main(cases):
         elif c == "c3_bc_h001":
             fwd_case(c, ising.ising_T0(synth.BETA_C, 1.0, 0.01), 64, 40,
                      dict(model="ising", beta=synth.BETA_C, J=1.0, h=0.01, d0=2))
+        elif c == "c1_ising":
+            grad_case(c, 0.44, 1.0, 0.0, 8, 20)
+        elif c == "c3_bc_h0_grad":
+            grad_case(c, synth.BETA_C, 1.0, 0.0, 64, 40)
+        elif c == "c3_bc_h001_grad":
+            grad_case(c, synth.BETA_C, 1.0, 0.01, 64, 40)
         elif c == "c2_grid":
             res = []
             t = time.time()

@@ -1,0 +1,66 @@
+"""Accuracy guard of the randomized subspace eigensolver (eigh_mode 1).
+
+After each subspace solve the kept Ritz pairs are checked on the device
+against the Gram matrix, r = max_a ||G v_a - theta_a v_a|| / theta_1; a step
+above the bound is recomputed, with every later step, by the exact partial
+eigensolver at the next synchronisation.  The isometry is the leading
+eigenvectors of the Gram matrix (SM Sec. B, isometry from the local HOSVD),
+so a solve that has not converged gives a different network; the guard must
+catch it and the final result must then agree with the oracle.
+"""
+import numpy as np
+import pytest
+
+import synth
+from oracle import hotrg
+
+hot = pytest.importorskip("paper_1912_02780_gb300")
+pytestmark = pytest.mark.gpu
+
+
+def test_guard_fires_on_an_unconverged_subspace_solve():
+    """A block of only D' + 1 vectors and one power iteration cannot resolve
+    the slowly decaying spectra of the first steps of a random tensor: the
+    guard fires, the failing steps are recomputed with the exact eigensolver
+    and ln Z/N agrees with the oracle (FP64 path).  With the guard switched off
+    (an unreachable bound) the same settings miss the oracle by far more."""
+    T0 = synth.random_symmetric_T0(0, 4)
+    d_cut, n = 16, 10
+    ref = hotrg.hotrg_forward(T0, d_cut, n, keep=False)
+    kw = dict(want_grad=False, eigh_mode=1, eigh_power_iters=1, eigh_block=d_cut + 1)
+    with hot.Plan(4, d_cut, n, "fp64", **kw) as p:
+        lnz, ln, _ = p.forward_tensor(T0)
+        res, exact, fb = p.eigh_diagnostics()
+    with hot.Plan(4, d_cut, n, "fp64", eigh_residual_tol=1e300, **kw) as p:
+        lnz_off, _, _ = p.forward_tensor(T0)
+        res_off, exact_off, fb_off = p.eigh_diagnostics()
+    err, err_off = abs(lnz - ref["lnz"]), abs(lnz_off - ref["lnz"])
+    print(f"guard on: |dlnz| = {err:.2e}, fallback steps {np.flatnonzero(exact) + 1}; "
+          f"guard off: |dlnz| = {err_off:.2e}, residuals {res_off}")
+    assert fb_off == 0 and not exact_off.any()
+    assert fb >= 1 and exact.any()
+    assert err < 1e-11
+    assert np.max(np.abs(ln - np.array(ref["log_norms"]))) < 1e-9
+    assert err_off > 100 * err
+
+
+def test_guard_state_resets_between_forwards_and_device_forward():
+    """The fallback flags belong to one forward; the device-resident forward
+    gives the same result once hotrg_sync has returned."""
+    import torch
+    T0 = synth.random_symmetric_T0(1, 4)
+    kw = dict(want_grad=False, eigh_mode=1, eigh_power_iters=1, eigh_block=17)
+    with hot.Plan(4, 16, 8, "fp64", **kw) as p:
+        lnz1, _, _ = p.forward_tensor(T0)
+        _, ex1, fb1 = p.eigh_diagnostics()
+        dev = torch.device("cuda", 0)
+        t = torch.tensor(T0, dtype=torch.float64, device=dev)
+        out = torch.zeros(10, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()
+        p.forward_device(t.data_ptr(), out.data_ptr())
+        p.sync()
+        lnz2 = float(out[0].item())
+        _, ex2, fb2 = p.eigh_diagnostics()
+    assert lnz1 == lnz2
+    assert np.array_equal(ex1, ex2)
+    assert fb2 == 2 * fb1

@@ -52,3 +52,41 @@ def test_ising_grid_against_stored_oracle():
     print(f"c2 grid: max |df| = {df.max():.2e}, max rel du = {du.max():.2e}")
     assert df.max() < 1e-9
     assert du.max() < 1e-6
+
+
+@pytest.mark.gpu
+def test_ising_grid_fp64_and_specific_heat_against_stored_oracle():
+    """C2 as specified: FP64 on the GPU (Ising, D_cut = 32, 30 steps), forward
+    and hand-written adjoint at 8 of the 64 grid points -- four consecutive
+    ones around the specific-heat peak next to beta_c, and four spread over
+    the grid -- against the oracle's stored ln Z/N and d(ln Z/N)/d beta:
+    |df| <= 1e-9 and |du| <= 1e-6 relative.  The specific heat
+    c = -beta^2 du/dbeta is compared at the two interior points of the
+    consecutive run, both sides by the same central difference of their own
+    u (the rule of observables.grid_derivative)."""
+    path = os.path.join(os.path.dirname(__file__), "golden", "c2_grid.json")
+    if not os.path.exists(path):
+        pytest.skip("golden c2_grid not generated")
+    g = json.load(open(path))
+    pts = g["points"]
+    run = [28, 29, 30, 31]                 # beta 0.433 .. 0.448, across beta_c = 0.4407
+    idx = [0, 15, 47, 63] + run
+    from paper_1912_02780_gb300.observables import ising_thermodynamics
+    betas = np.array([pts[i]["beta"] for i in idx])
+    res = ising_thermodynamics(betas, g["d_cut"], g["n_steps"], "fp64")
+    lnz_ref = np.array([pts[i]["lnz"] for i in idx])
+    u_ref = -np.array([pts[i]["dlnz_dbeta"] for i in idx])
+    df = np.abs(res["lnz"] - lnz_ref) / betas
+    du = np.abs(res["u"] - u_ref) / np.abs(u_ref)
+    # specific heat on the consecutive run (positions 4..7 of idx)
+    h = pts[1]["beta"] - pts[0]["beta"]
+    u_run, u_run_ref, b_run = res["u"][4:], u_ref[4:], betas[4:]
+    c = -b_run[1:-1] ** 2 * (u_run[2:] - u_run[:-2]) / (2 * h)
+    c_ref = -b_run[1:-1] ** 2 * (u_run_ref[2:] - u_run_ref[:-2]) / (2 * h)
+    dc = np.abs(c - c_ref) / np.abs(c_ref)
+    print(f"c2 grid fp64: max |df| = {df.max():.2e}, max rel du = {du.max():.2e}, "
+          f"c = {c}, max rel dc = {dc.max():.2e}")
+    assert df.max() < 1e-9
+    assert du.max() < 1e-6
+    assert dc.max() < 1e-6
+    assert np.all(c > 0)
