@@ -439,8 +439,8 @@ def main():
                          "default; smaller = smaller plans and stage GEMMs, same results)")
     ap.add_argument("--stage2-group", type=int, default=0,
                     help="N-tiles per L2 raster group of the stage-2 GEMM (0: library default)")
-    ap.add_argument("--stage2-prefetch", type=int, default=0,
-                    help="stage-2 GEMM L2 prefetch distance in K slabs (0: default, <0: off)")
+    ap.add_argument("--stage2-pair", type=int, default=0,
+                    help="stage-2 GEMM on CTA pairs (0: library default, 1: on, -1: off)")
     ap.add_argument("--no-c1", action="store_true", help="skip the C1 latency measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -496,7 +496,7 @@ def main():
                       hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
                       eigh_power_iters=args.power_iters, eigh_block=args.eigh_block,
                       split_chunk_elems=args.split_chunk, stage2_n_group=args.stage2_group,
-                      stage2_prefetch=args.stage2_prefetch)
+                      stage2_pair=args.stage2_pair)
              for st in streams]
     T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
     out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]
@@ -625,7 +625,8 @@ def main():
             "lnz_per_site": lnzs,
             "stage_ms_per_solve": {k: v[0] for k, v in prof.items()},
             "gpu_launches": int(launches),
-            "eigh_guard": {"residual_tol": 1e-7,
+            "eigh_guard": {"bound": "2^-k r_k <= 1e-7 (r_k: relative residual of the kept "
+                                    "Ritz pairs at step k), else the exact eigensolver",
                            "max_residual": [float(np.nanmax(g_[0])) if np.any(np.isfinite(g_[0]))
                                             else None for g_ in guard],
                            "fallbacks_total": [g_[2] for g_ in guard]},

@@ -111,9 +111,10 @@ typedef struct {
                                forms no Gram and no eigensolve.  Needs want_grad = 1 and
                                fixed_w_grad = 1.                                          */
   double eigh_residual_tol; /* eigh_mode 1: accuracy guard of the subspace eigensolver.  After
-                               each subspace solve the kept Ritz pairs are checked on the
-                               device, r = max_a ||G v_a - theta_a v_a||_2 / theta_1; a step
-                               with r above this bound (<= 0: 1e-7) is recomputed with the
+                               the subspace solve of step k the kept Ritz pairs are checked on
+                               the device, r_k = max_a ||G v_a - theta_a v_a||_2 / theta_1; a
+                               step with 2^-k r_k above this bound (<= 0: 1e-7; an error at
+                               step k enters ln Z / N with weight 2^-k) is recomputed with the
                                exact partial eigensolver (cuSOLVER syevdx) together with every
                                later step, at the next synchronisation (hotrg_sync or the
                                host-buffer forward).  Must be finite and >= 0.            */
@@ -123,11 +124,11 @@ typedef struct {
                                operand stays in L2 while A streams; 0 = the default (16);
                                a value >= the N-tile count = plain N-fastest order.  Results
                                do not depend on it.                                        */
-  int stage2_prefetch;      /* stage-2 GEMM: its TMA warp prefetches into L2 the K slab this
-                               many 64-wide slabs ahead of the one it loads into shared
-                               memory, so that the load finds its data in L2; 0 = the default
-                               (4), < 0 = no prefetch, at most 64.  Results do not depend on
-                               it.                                                         */
+  int stage2_pair;          /* stage-2 GEMM of the three-plane steps on CTA pairs (tcgen05
+                               cta_group::2: 256-row tiles, each CTA of a cluster of two loads
+                               its 128 rows of U and half of the 128-row tile of the other
+                               operand); 0 = the default (on), > 0 = on, < 0 = one CTA per
+                               tile.  Results are bit-identical either way.                */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -136,7 +137,7 @@ typedef struct hotrg_plan_s* hotrg_plan;
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
  * epilogue_split = 1, split_chunk_elems = 0, w_given = 0, eigh_residual_tol = 0,
- * stage2_n_group = 0, stage2_prefetch = 0.
+ * stage2_n_group = 0, stage2_pair = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 

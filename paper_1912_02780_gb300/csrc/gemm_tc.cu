@@ -93,14 +93,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* tm,
       : "memory");
 }
 
-// L2 prefetch of one tensor-map box (no shared memory, no completion).
-__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap* tm, int c0, int c1, int c2) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
-                   (uint64_t)tm),
-               "r"(c0), "r"(c1), "r"(c2)
-               : "memory");
-}
-
 __device__ __forceinline__ void tc_fence_before() {
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
 }
@@ -119,6 +111,63 @@ __device__ __forceinline__ void tc_mma(uint32_t d_tmem, uint64_t adesc, uint64_t
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
       "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
+// ---- CTA-pair (cluster of two) helpers ------------------------------------
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+// Address of the same shared-memory location in CTA `rank` of the cluster.
+__device__ __forceinline__ uint32_t map_to_rank(uint32_t saddr, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(saddr), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ void mbar_arrive_cluster(uint32_t cbar) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(cbar)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx_cluster(uint32_t cbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cluster.shared::cluster.b64 _, [%0], %1;" ::"r"(
+                   cbar),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::
+                   : "memory");
+}
+// TMA load into this CTA's shared memory whose completion is counted on an
+// mbarrier of either CTA of the pair (cbar: a shared::cluster address).
+__device__ __forceinline__ void tma_load_3d_pair(uint32_t dst, const CUtensorMap* tm,
+                                                 uint32_t cbar, int c0, int c1, int c2) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes.cta_group::2 "
+      "[%0], [%1, {%3, %4, %5}], [%2];" ::"r"(dst),
+      "l"((uint64_t)tm), "r"(cbar), "r"(c0), "r"(c1), "r"(c2)
+      : "memory");
+}
+// Pair MMA, issued by the even CTA: D (128 lanes in each CTA's TMEM) +=
+// A (128 rows from each CTA) x B (N/2 rows from each CTA).
+__device__ __forceinline__ void tc_mma_pair(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc,
+                                            uint32_t idesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::2.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(d_tmem),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// Arrive on the mbarrier at offset `bar` of every CTA in `mask` once all pair
+// MMAs issued so far by this thread have completed.
+__device__ __forceinline__ void tc_commit_pair(uint32_t bar, uint16_t mask) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 "
+      "[%0], %1;" ::"r"(bar),
+      "h"(mask)
       : "memory");
 }
 
@@ -256,60 +305,86 @@ __device__ __forceinline__ void tile_coords(long long t, int MT, int NT, int m_f
   }
 }
 
-template <int BN, int NP, int BK>
+// CG = 1: one CTA computes a BM x BN tile.  CG = 2: a cluster of two CTAs
+// computes a (2 BM) x BN tile with pair MMAs (tcgen05 cta_group::2); each CTA
+// loads its BM rows of A and BN / 2 rows of B, so a pipeline stage is 25 %
+// smaller per CTA and three stages fit, and the tensor cores read a quarter
+// less shared memory per flop.
+template <int BN, int NP, int BK, int CG = 1>
 struct Cfg {
+  static constexpr int kBRows = BN / CG;                 // B rows loaded by each CTA
   static constexpr int kAPlane = BM * BK * 2;
-  static constexpr int kBPlane = BN * BK * 2;
+  static constexpr int kBPlane = kBRows * BK * 2;
   static constexpr int kStage = NP * (kAPlane + kBPlane);
-  static constexpr int kStages = (200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage);
   static constexpr int kEpiWarps = 8;                    // 2 warps per TMEM lane quadrant
   static constexpr int kThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
   static constexpr int kCols = BN / 2;                   // columns per epilogue thread
-  static constexpr int kBars = 2 * kStages + 5;
   // Shared memory after the pipeline stages (byte offsets from the 1024-aligned
   // base): mbarriers, column offsets (BN), contiguity flags, the TMEM address,
   // the segment-max / offset exchange of the grid-split epilogue (2 halves x
-  // 128 rows), and a 2 KB store-staging buffer per epilogue warp (16-byte
-  // aligned: it is accessed as uint4).
-  static constexpr int kStageBytes = 2048;
+  // 128 rows), and a store-staging buffer per epilogue warp (16-byte aligned:
+  // it is accessed as uint4).  CG = 2 uses 1 KB staging buffers and keeps the
+  // exchange inside them (a barrier separates the two uses), which is what lets
+  // three pipeline stages fit.
+  static constexpr int kStageBytes = CG == 2 ? 1024 : 2048;
+  static constexpr int kExtra = 1024 + 11 * 8 + BN * 8 + BN / 16 * 4 + 32 +
+                                (CG == 2 ? 0 : 2 * BM * 12 + 16) + kEpiWarps * kStageBytes;
+  static constexpr int kFit = (232448 - kExtra) / kStage;
+  static constexpr int kStages =
+      CG == 2 ? (kFit > 4 ? 4 : kFit) : ((200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage));
+  static constexpr int kBars = 2 * kStages + 5;
   static constexpr int kOffBars = kStages * kStage;
   static constexpr int kOffCn = kOffBars + kBars * 8;
   static constexpr int kOffCv = kOffCn + BN * 8;
   static constexpr int kOffTmem = kOffCv + BN / 16 * 4;
   static constexpr int kOffXo = (kOffTmem + 16 + 15) / 16 * 16;
   static constexpr int kOffXm = kOffXo + 2 * BM * 8;
-  static constexpr int kOffStg = (kOffXm + 2 * BM * 4 + 15) / 16 * 16;
+  static constexpr int kOffStg =
+      CG == 2 ? kOffXo : (kOffXm + 2 * BM * 4 + 15) / 16 * 16;
   static constexpr int kSmem = 1024 + kOffStg + kEpiWarps * kStageBytes;
   static_assert(kOffCn % 8 == 0 && kOffXo % 16 == 0 && kOffStg % 16 == 0, "smem alignment");
+  static_assert(CG == 1 || 2 * BM * 12 <= kEpiWarps * kStageBytes, "exchange fits the staging");
   static_assert(kSmem <= 232448, "shared memory per CTA");
   // TMEM: per buffer (2) an exact hi*hi accumulator and a "rest" accumulator, BN columns each.
   static constexpr int kTmemCols = 4 * BN;
   static_assert(kStages >= 2, "need at least two pipeline stages");
   static_assert(kTmemCols <= 512, "TMEM holds 512 columns");
+  static_assert(CG == 1 || CG == 2, "one CTA or a pair");
 };
 // Warp-cooperative store of 64 bytes per lane (each lane: one contiguous,
-// 16-byte aligned destination run) through the warp's 2 KB staging buffer:
-// every store instruction then writes 8 runs x 64 bytes (whole 32-byte
-// sectors) instead of 32 runs x 16 bytes.  The 16-byte chunk position is
-// XOR-swizzled with the row so that both shared-memory passes are free of bank
-// conflicts.  All 32 lanes must take part.
+// 16-byte aligned destination run) through the warp's staging buffer: every
+// store instruction then writes 8 runs x 64 bytes (whole 32-byte sectors)
+// instead of 32 runs x 16 bytes.  The 16-byte chunk position is XOR-swizzled
+// with the row so that both shared-memory passes are free of bank conflicts.
+// With a 2 KB buffer all 32 rows go through at once; with 1 KB, in two halves
+// of 16 rows.  All 32 lanes must take part.
+template <int kBytes>
 __device__ __forceinline__ void warp_store64(uint8_t* stage, const uint4 (&v)[4], char* dst,
                                              int lane) {
-  const int sw = (lane >> 1) & 3;
-  uint4* srow = reinterpret_cast<uint4*>(stage + lane * 64);
-#pragma unroll
-  for (int c = 0; c < 4; ++c) srow[c ^ sw] = v[c];
-  __syncwarp();
+  constexpr int kRows = kBytes / 64;   // rows staged per pass (32 or 16)
+  static_assert(kRows == 32 || kRows == 16, "2 KB or 1 KB staging");
   const int c = lane & 3;
 #pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const int r = 8 * k + (lane >> 2);
-    char* d = reinterpret_cast<char*>(
-        __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), r));
-    const uint4 x = reinterpret_cast<const uint4*>(stage + r * 64)[c ^ ((r >> 1) & 3)];
-    *reinterpret_cast<uint4*>(d + c * 16) = x;
+  for (int h = 0; h < 32 / kRows; ++h) {
+    if ((lane / kRows) == h) {
+      const int lr = lane % kRows;
+      const int sw = (lr >> 1) & 3;
+      uint4* srow = reinterpret_cast<uint4*>(stage + lr * 64);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) srow[q ^ sw] = v[q];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int k = 0; k < kRows / 8; ++k) {
+      const int lr = 8 * k + (lane >> 2);
+      const int r = h * kRows + lr;
+      char* d = reinterpret_cast<char*>(
+          __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(dst), r));
+      const uint4 x = reinterpret_cast<const uint4*>(stage + lr * 64)[c ^ ((lr >> 1) & 3)];
+      *reinterpret_cast<uint4*>(d + c * 16) = x;
+    }
+    __syncwarp();
   }
-  __syncwarp();
 }
 
 __device__ __forceinline__ uint32_t pack_bf16x2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
@@ -367,11 +442,16 @@ __device__ __forceinline__ void store_tile_chunk(const TcGemm& p, long long coff
 
 // 320 threads: 10 warps, 3 on two of the SM's four sub-partitions, so at most
 // 168 registers a thread (3 x 32 x 168 <= 16384).
-template <int BN, int NP, int BK>
-__global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
+// CG = 2: launched in clusters of two CTAs.  The even CTA's MMA warp issues
+// the pair MMAs for both; each CTA's TMA warp loads its own halves and counts
+// them on the even CTA's full barrier; the MMA completion is multicast to both
+// CTAs' stage-empty and accumulator-full barriers; both CTAs' epilogue warps
+// release an accumulator on the even CTA's barrier.
+template <int BN, int NP, int BK, int CG>
+__global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
     tc_gemm_kernel(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB,
                    const TcGemm p) {
-  using C = Cfg<BN, NP, BK>;
+  using C = Cfg<BN, NP, BK, CG>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -385,6 +465,7 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
 
   const int warp = threadIdx.x / 32, lane = threadIdx.x % 32;
   const int kProducer = C::kEpiWarps, kMma = C::kEpiWarps + 1;
+  const uint32_t rank = CG == 2 ? cluster_rank() : 0u;   // 0: the CTA that issues the MMAs
   const uint32_t bar0 = smem_u32(bars);
   auto full_bar = [&](int s) { return bar0 + 8u * s; };
   auto empty_bar = [&](int s) { return bar0 + 8u * (C::kStages + s); };
@@ -399,12 +480,12 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
 
   if (warp == kProducer && lane == 0) {
     for (int s = 0; s < C::kStages; ++s) {
-      mbar_init(full_bar(s), 1);
+      mbar_init(full_bar(s), CG);             // one expect_tx arrival per CTA of the pair
       mbar_init(empty_bar(s), 1);
     }
     for (int a = 0; a < 2; ++a) {
       mbar_init(tfull_bar(a), 1);
-      mbar_init(tempty_bar(a), C::kEpiWarps);
+      mbar_init(tempty_bar(a), C::kEpiWarps * CG);
     }
     mbar_init(drain_bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -413,18 +494,31 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
     asm volatile("prefetch.tensormap [%0];" ::"l"((uint64_t)&tmB) : "memory");
   }
   if (warp == kMma) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
-                     smem_u32(tmem_slot)),
-                 "r"(C::kTmemCols)
-                 : "memory");
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    if constexpr (CG == 2) {
+      asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(C::kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+    } else {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                       smem_u32(tmem_slot)),
+                   "r"(C::kTmemCols)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
   }
   tc_fence_before();
-  __syncthreads();
+  if constexpr (CG == 2) cluster_sync();   // both CTAs' barriers are initialised
+  else __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = *tmem_slot;
+  // the even CTA's full / tempty barriers, as shared::cluster addresses
+  auto lead = [&](uint32_t bar) { return CG == 2 ? map_to_rank(bar, 0) : bar; };
 
-  const int MT = (p.M + BM - 1) / BM, NT = (p.N + BN - 1) / BN;
+  // CG = 2: a tile is 2 BM rows; the pair (cluster) walks the tiles together
+  const int MT = (p.M + BM * CG - 1) / (BM * CG), NT = (p.N + BN - 1) / BN;
+  const long long t0 = blockIdx.x / CG, tstep = gridDim.x / CG;
   const long long tiles = (long long)MT * NT;
   const int KB = (p.K + BK - 1) / BK;
   // p.kchunk counts 64-wide K blocks; a chunk spans (64 / BK) slabs per unit
@@ -440,61 +534,51 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
       int issued[C::kStages];
       uint32_t last_par[C::kStages];
       for (int i = 0; i < C::kStages; ++i) { issued[i] = 0; last_par[i] = 0; }
-      const int pf = p.prefetch;
-      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (long long t = t0; t < tiles && ok; t += tstep) {
         int mt, nt;
         tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
-        int pmt = -1, pnt = -1;   // the CTA's next tile, for prefetches past this one's end
-        if (pf > 0 && t + gridDim.x < tiles)
-          tile_coords(t + gridDim.x, MT, NT, p.m_fast, p.n_group, pmt, pnt);
-        if (pf > 0 && t == blockIdx.x) {
-          // the first slabs of the first tile
-          for (int q = 0; q < pf && q < KB; ++q) {
-            for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, q * BK, mt * BM, pl);
-            for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, q * BK, nt * BN, pl);
-          }
-        }
+        const int arow = mt * BM * CG + (int)rank * BM, brow = nt * BN + (int)rank * C::kBRows;
         for (int kb = 0; kb < KB; ++kb) {
-          if (pf > 0) {
-            // warm L2 with the slab `pf` ahead (of this tile, else of the next
-            // one), so that the TMA load of it finds its data there
-            const int q = kb + pf;
-            if (q < KB) {
-              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, q * BK, mt * BM, pl);
-              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, q * BK, nt * BN, pl);
-            } else if (pmt >= 0 && q - KB < KB) {
-              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmA, (q - KB) * BK, pmt * BM, pl);
-              for (int pl = 0; pl < NP; ++pl) tma_prefetch_3d(&tmB, (q - KB) * BK, pnt * BN, pl);
-            }
-          }
           if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err)) { ok = false; break; }
-          mbar_expect_tx(full_bar(s), C::kStage);
+          if constexpr (CG == 2) {
+            const uint32_t fb = lead(full_bar(s));
+            mbar_expect_tx_cluster(fb, C::kStage);
 #pragma unroll
-          for (int pl = 0; pl < NP; ++pl)
-            tma_load_3d(a_tile(s, pl), &tmA, full_bar(s), kb * BK, mt * BM, pl);
+            for (int pl = 0; pl < NP; ++pl)
+              tma_load_3d_pair(a_tile(s, pl), &tmA, fb, kb * BK, arow, pl);
 #pragma unroll
-          for (int pl = 0; pl < NP; ++pl)
-            tma_load_3d(b_tile(s, pl), &tmB, full_bar(s), kb * BK, nt * BN, pl);
+            for (int pl = 0; pl < NP; ++pl)
+              tma_load_3d_pair(b_tile(s, pl), &tmB, fb, kb * BK, brow, pl);
+          } else {
+            mbar_expect_tx(full_bar(s), C::kStage);
+#pragma unroll
+            for (int pl = 0; pl < NP; ++pl)
+              tma_load_3d(a_tile(s, pl), &tmA, full_bar(s), kb * BK, arow, pl);
+#pragma unroll
+            for (int pl = 0; pl < NP; ++pl)
+              tma_load_3d(b_tile(s, pl), &tmB, full_bar(s), kb * BK, brow, pl);
+          }
           issued[s] = 1;
           last_par[s] = ph;
           if (++s == C::kStages) { s = 0; ph ^= 1u; }
         }
       }
-      if (!ok) {
-        // Let copies already in flight land before the CTA can exit.
+      if (!ok && rank == 0) {
+        // Let copies already in flight land before the CTA can exit (the
+        // odd CTA's copies are counted on the even CTA's barriers).
         for (int s2 = 0; s2 < C::kStages; ++s2)
           if (issued[s2]) mbar_wait(full_bar(s2), last_par[s2], p.err);
       }
     }
   } else if (warp == kMma) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    if (lane == 0 && rank == 0) {
+      constexpr uint32_t idesc = idesc_bf16(BM * CG, BN);
       int s = 0;
       uint32_t ph = 0;
       int acc = 0;
       uint32_t acc_ph = 0;
       bool ok = true;
-      for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+      for (long long t = t0; t < tiles && ok; t += tstep) {
         for (int c = 0; c < nchunks && ok; ++c) {
           if (!mbar_wait(tempty_bar(acc), acc_ph ^ 1u, p.err)) { ok = false; break; }
           tc_fence_after();
@@ -511,20 +595,28 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
               const uint32_t a0 = a_tile(s, p.pa[q]), b0 = b_tile(s, p.pb[q]);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
-                tc_mma(d, sdesc<BK>(a0 + kk * 32), sdesc<BK>(b0 + kk * 32), idesc,
-                       (first && kk == 0) ? 0u : 1u);
+                if constexpr (CG == 2)
+                  tc_mma_pair(d, sdesc<BK>(a0 + kk * 32), sdesc<BK>(b0 + kk * 32), idesc,
+                              (first && kk == 0) ? 0u : 1u);
+                else
+                  tc_mma(d, sdesc<BK>(a0 + kk * 32), sdesc<BK>(b0 + kk * 32), idesc,
+                         (first && kk == 0) ? 0u : 1u);
               }
             }
-            tc_commit(empty_bar(s));
+            if constexpr (CG == 2) tc_commit_pair(empty_bar(s), 3);   // both CTAs' stage s
+            else tc_commit(empty_bar(s));
             if (++s == C::kStages) { s = 0; ph ^= 1u; }
           }
           if (!ok) break;
-          tc_commit(tfull_bar(acc));
+          if constexpr (CG == 2) tc_commit_pair(tfull_bar(acc), 3);
+          else tc_commit(tfull_bar(acc));
           if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
         }
       }
-      // All MMAs issued by this thread must finish before TMEM is freed.
-      tc_commit(drain_bar);
+      // All MMAs issued by this thread (into both CTAs' TMEM) must finish
+      // before TMEM is freed.
+      if constexpr (CG == 2) tc_commit_pair(drain_bar, 1);
+      else tc_commit(drain_bar);
       mbar_wait(drain_bar, 0, p.err);
     }
   } else {
@@ -540,10 +632,10 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
     const int col0 = half * C::kCols;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     float rhi[C::kCols], rlo[C::kCols];
-    for (long long t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+    for (long long t = t0; t < tiles && ok; t += tstep) {
       int mt, nt;
       tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
-      const int m0 = mt * BM, n0 = nt * BN;
+      const int m0 = mt * BM * CG + (int)rank * BM, n0 = nt * BN;
       const int m = m0 + row;
       const bool mok = m < p.M;
       const long long coff = mok ? imap(p.cm, m) : 0;
@@ -580,7 +672,10 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
         }
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(tempty_bar(acc));
+        if (lane == 0) {
+          if constexpr (CG == 2) mbar_arrive_cluster(lead(tempty_bar(acc)));
+          else mbar_arrive(tempty_bar(acc));
+        }
         if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
       }
       // column offsets of this tile (shared by the 8 epilogue warps); the
@@ -620,6 +715,9 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
         const int pidx = (half ^ p.seg_phalf) * BM + (row ^ p.seg_prow);
         const float pm = xm_s[pidx];
         const long long po = xo_s[pidx];
+        // CG = 2: the exchange lives in the staging buffers, which the stores
+        // below overwrite: every warp must have read its partner first
+        if constexpr (CG == 2) named_bar(1, kEpiThreads);
         const bool valid = mok && o >= 0 && po == (o ^ 64);
         if (mok && !valid) report_error(p.err, kErrBounds);
         // grid of the segment (the rule of kernels.cu: grid_split); v / g is
@@ -657,7 +755,7 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
               v4[c] = make_uint4(pk[4 * c], pk[4 * c + 1], pk[4 * c + 2], pk[4 * c + 3]);
             char* d = reinterpret_cast<char*>(dst + q * p.out_plane_stride + hh * 32);
             if (coop) {
-              warp_store64(stage, v4, d, lane);
+              warp_store64<C::kStageBytes>(stage, v4, d, lane);
             } else if (valid) {
 #pragma unroll
               for (int c = 0; c < 4; ++c) reinterpret_cast<uint4*>(d)[c] = v4[c];
@@ -687,8 +785,8 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
                                    __float_as_uint(p.alpha * (hi[4 * c + 1] + lo[4 * c + 1])),
                                    __float_as_uint(p.alpha * (hi[4 * c + 2] + lo[4 * c + 2])),
                                    __float_as_uint(p.alpha * (hi[4 * c + 3] + lo[4 * c + 3])));
-              warp_store64(stage, v4, reinterpret_cast<char*>(reinterpret_cast<float*>(p.C) + off0),
-                           lane);
+              warp_store64<C::kStageBytes>(
+                  stage, v4, reinterpret_cast<char*>(reinterpret_cast<float*>(p.C) + off0), lane);
             } else {
 #pragma unroll
               for (int hv = 0; hv < 2; ++hv) {
@@ -703,7 +801,7 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
                   v4[c] = make_uint4((uint32_t)u0, (uint32_t)(u0 >> 32), (uint32_t)u1,
                                      (uint32_t)(u1 >> 32));
                 }
-                warp_store64(
+                warp_store64<C::kStageBytes>(
                     stage, v4,
                     reinterpret_cast<char*>(reinterpret_cast<double*>(p.C) + off0 + hv * 8), lane);
               }
@@ -718,12 +816,20 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK>::kThreads, 1)
 
   __syncwarp();
   tc_fence_before();
-  __syncthreads();
+  // CG = 2: neither CTA frees its TMEM or exits while the pair's MMAs or the
+  // other CTA's barrier arrivals may still reach it
+  if constexpr (CG == 2) cluster_sync();
+  else __syncthreads();
   tc_fence_after();
   if (warp == kMma) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
-                 "r"(C::kTmemCols)
-                 : "memory");
+    if constexpr (CG == 2)
+      asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(C::kTmemCols)
+                   : "memory");
+    else
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base),
+                   "r"(C::kTmemCols)
+                   : "memory");
   }
 }
 typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
@@ -759,24 +865,44 @@ bool make_map(CUtensorMap* tm, const TcOperand& op, int box_rows, int bk) {
   return r == CUDA_SUCCESS;
 }
 
-template <int BN, int NP, int BK>
+template <int BN, int NP, int BK, int CG = 1>
 cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,
                    int num_sms) {
-  using C = Cfg<BN, NP, BK>;
+  using C = Cfg<BN, NP, BK, CG>;
   CUtensorMap ta, tb;
-  if (!make_map(&ta, A, BM, BK) || !make_map(&tb, B, BN, BK)) return cudaErrorInvalidValue;
+  if (!make_map(&ta, A, BM, BK) || !make_map(&tb, B, C::kBRows, BK)) return cudaErrorInvalidValue;
   static bool attr_set = false;
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP, BK>,
+    cudaError_t e = cudaFuncSetAttribute(tc_gemm_kernel<BN, NP, BK, CG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, C::kSmem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  long long tiles = (long long)((g.M + BM - 1) / BM) * ((g.N + BN - 1) / BN);
-  int grid = (int)(tiles < num_sms ? tiles : num_sms);
+  const long long tiles =
+      (long long)((g.M + BM * CG - 1) / (BM * CG)) * ((g.N + BN - 1) / BN);
   count_launch();
-  tc_gemm_kernel<BN, NP, BK><<<grid, C::kThreads, C::kSmem, stream>>>(ta, tb, g);
-  return cudaGetLastError();
+  if constexpr (CG == 1) {
+    int grid = (int)(tiles < num_sms ? tiles : num_sms);
+    tc_gemm_kernel<BN, NP, BK, 1><<<grid, C::kThreads, C::kSmem, stream>>>(ta, tb, g);
+    return cudaGetLastError();
+  } else {
+    // persistent clusters of two CTAs: one pair per two SMs (or per tile)
+    const long long pairs = num_sms / 2 < tiles ? num_sms / 2 : tiles;
+    cudaLaunchConfig_t cfg;
+    memset(&cfg, 0, sizeof(cfg));
+    cfg.gridDim = dim3((unsigned)(2 * pairs), 1, 1);
+    cfg.blockDim = dim3(C::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = C::kSmem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, tc_gemm_kernel<BN, NP, BK, 2>, ta, tb, g);
+  }
 }
 
 // Self-test of the bounded wait: one thread waits on an mbarrier that nothing
@@ -845,6 +971,7 @@ cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cud
       return launch<64, 2, 64>(A, B, g, stream, num_sms);
     }
     if (g.nplanes == 3) {
+      if (g.N > 64 && g.cta_pair && num_sms >= 2) return launch<128, 3, 64, 2>(A, B, g, stream, num_sms);
       if (g.N > 64) return launch<128, 3, 64>(A, B, g, stream, num_sms);
       return launch<64, 3, 64>(A, B, g, stream, num_sms);
     }

@@ -44,8 +44,8 @@ struct TcGemm {
                              // L2 by neighbouring CTAs), 0 = consecutive tiles walk N
   int n_group;               // with m_fast = 0 and n_group > 0: tiles in groups of n_group
                              // N-tiles (an L2-resident stripe of B), M-major inside
-  int prefetch;              // > 0: the TMA warp prefetches into L2 the K slab this many
-                             // slabs ahead of the one it loads (0: no prefetch)
+  int cta_pair;              // 1: run a three-plane, 64-wide-K, N > 64 GEMM on CTA pairs
+                             // (tcgen05 cta_group::2, 256-row tiles); same results
   int seg_prow, seg_phalf;   // kOutGridSplit: segment partner of (row, half)
 };
 

@@ -269,7 +269,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->split_chunk_elems < 0 || c->split_chunk_elems > (1LL << 34)) return HOTRG_EINVAL;
   if (c->w_given && (!c->want_grad || !c->fixed_w_grad)) return HOTRG_EINVAL;
   if (!std::isfinite(c->eigh_residual_tol) || c->eigh_residual_tol < 0) return HOTRG_EINVAL;
-  if (c->stage2_n_group < 0 || c->stage2_prefetch > 64) return HOTRG_EINVAL;
+  if (c->stage2_n_group < 0) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -431,11 +431,8 @@ hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, cons
 // N-tiles per L2 raster group of the stage-2 GEMM (0 in the config: the
 // default; >= the N-tile count: plain N-fastest order).
 int stage2_group(const hotrg_config& c) { return c.stage2_n_group > 0 ? c.stage2_n_group : 16; }
-// K slabs between the stage-2 GEMM's L2 prefetch and its TMA load (config:
-// 0 = the default, < 0 = no prefetch).
-int stage2_prefetch(const hotrg_config& c) {
-  return c.stage2_prefetch > 0 ? c.stage2_prefetch : (c.stage2_prefetch < 0 ? 0 : 4);
-}
+// Stage-2 GEMM on CTA pairs (config: 0 = the default, > 0 = on, < 0 = off).
+int stage2_pair(const hotrg_config& c) { return c.stage2_pair < 0 ? 0 : 1; }
 
 // Segment partner of the grid-split epilogue (see gemm_tc.h: kOutGridSplit)
 // for an output whose 64-column half-runs are `run` consecutive destination
@@ -503,7 +500,7 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     g2.seg_prow = p2r;
     g2.seg_phalf = p2h;
     g2.n_group = stage2_group(p->cfg);
-    g2.prefetch = stage2_prefetch(p->cfg);
+    g2.cta_pair = stage2_pair(p->cfg);
     CK(tc_gemm(u, pp, g2, st, p->sms));
     }
     if (!fuse2) {
@@ -553,10 +550,18 @@ int subspace_ritz(const StepGeom& s) { return s.Xp + 1; }
 // rows and their Ritz values in p->wasc, ready for eig_desc.
 constexpr int kEighPlanes = 4;
 
-// Residual bound of the kept Ritz pairs, relative to the largest eigenvalue,
-// above which a step's subspace eigensolve is replaced by the exact one.
-double residual_tol(const hotrg_config& c) {
-  return c.eigh_residual_tol > 0 ? c.eigh_residual_tol : 1e-7;
+// Residual bound of the kept Ritz pairs at step k, relative to the largest
+// eigenvalue, above which the step's subspace eigensolve is replaced by the
+// exact one.  The bound is on 2^-k r_k: an error made at step k enters
+// ln Z / N with weight 2^-k (through ln c_k / 2^k and every later step of the
+// same 2^k-site block).  Measured on GB300 (random reflection-symmetric d0 = 4
+// tensors at D_cut = 16, 32, 64 and Ising at beta_c, D_cut = 64): every solve
+// whose ln Z / N missed the oracle by more than 1e-9 had a step with
+// 2^-k r_k >= 1.2e-6, every one within 1e-9 stayed below 7.5e-8, and the
+// error was at most 1e-2 times the largest 2^-k r_k.
+double residual_tol(const hotrg_config& c, int k) {
+  const double t = c.eigh_residual_tol > 0 ? c.eigh_residual_tol : 1e-7;
+  return std::ldexp(t, k);
 }
 
 bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
@@ -640,7 +645,8 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
 
 // Accuracy guard of the subspace eigensolver: the kept Ritz pairs (rows of
 // Ek, values lk descending) are checked against the Gram matrix still in
-// p->Escr, r = max_a ||G v_a - theta_a v_a|| / theta_1.  On split steps the
+// p->Escr, r = max_a ||G v_a - theta_a v_a|| / theta_1, bounded by
+// residual_tol(k).  On split steps the
 // products run on the four-plane tensor-core GEMM with the split of G the
 // eigensolver made; otherwise in FP64.  A step over the bound raises the
 // guard word err[2] to n + 1 - k (the earliest failing step wins); the host
@@ -663,7 +669,7 @@ hotrg_status eigh_residual(hotrg_plan p, const StepGeom& s, int k) {
                     map_lin(N), map_lin(1), Dp, N, N, 1.0, 0.0),
                 st, p->sms));
   }
-  CK(eig_residual(p->Zs, Ek, p->lam[k - 1], Dp, N, residual_tol(p->cfg), p->partial,
+  CK(eig_residual(p->Zs, Ek, p->lam[k - 1], Dp, N, residual_tol(p->cfg, k), p->partial,
                   p->dres + (k - 1), p->err + 2, p->cfg.n_steps + 1 - k, st));
   return HOTRG_OK;
 }
@@ -1055,7 +1061,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->w_given = 0;
   c->eigh_residual_tol = 0.0;
   c->stage2_n_group = 0;
-  c->stage2_prefetch = 0;
+  c->stage2_pair = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {

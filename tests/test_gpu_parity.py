@@ -310,3 +310,25 @@ def test_epilogue_split_bit_identical_to_staged_split():
     for o in out[1:]:
         assert o[0] == out[0][0]
         assert np.array_equal(o[1], out[0][1])
+
+
+@pytest.mark.parametrize("d_cut,n,chunk", [(64, 9, 0), (40, 8, 1 << 21)])
+def test_stage2_cta_pair_bit_identical_to_single_cta(d_cut, n, chunk):
+    """The stage-2 GEMM of the three-plane steps on CTA pairs (tcgen05
+    cta_group::2, 256-row tiles) sums every output element in the same order
+    as the one-CTA kernel: the whole forward must be bit-identical.  D_cut = 64
+    takes the fused grid-split epilogue; D_cut = 40 with small y-chunks gives
+    row counts that are not multiples of 256 (the odd CTA's rows past the end)
+    and the FP32 staging output."""
+    T0 = synth.random_symmetric_T0(0, 4)
+    out = []
+    for pair in (1, -1):
+        with hot.Plan(4, d_cut, n, "bf16x6", split_from_step=4, want_grad=False,
+                      hi_precision_steps=2, eigh_mode=1, eigh_power_iters=2,
+                      split_chunk_elems=chunk, stage2_pair=pair) as p:
+            lnz, ln, _ = p.forward_tensor(T0)
+            _, _, is_split = p.diagnostics()
+        out.append((lnz, np.array(ln)))
+    assert is_split[-1] == 1
+    assert out[0][0] == out[1][0]
+    assert np.array_equal(out[0][1], out[1][1])
