@@ -112,12 +112,13 @@ typedef struct {
                                fixed_w_grad = 1.                                          */
   double eigh_residual_tol; /* eigh_mode 1: accuracy guard of the subspace eigensolver.  After
                                the subspace solve of step k the kept Ritz pairs are checked on
-                               the device, r_k = max_a ||G v_a - theta_a v_a||_2 / theta_1; a
-                               step with 2^-k r_k above this bound (<= 0: 1e-7; an error at
-                               step k enters ln Z / N with weight 2^-k) is recomputed with the
-                               exact partial eigensolver (cuSOLVER syevdx) together with every
-                               later step, at the next synchronisation (hotrg_sync or the
-                               host-buffer forward).  Must be finite and >= 0.            */
+                               the device, r_k = max_a ||G v_a - theta_a v_a||_2 / theta_1.
+                               Where 2^-k r_k exceeds this bound (<= 0: 5e-9; an error at step
+                               k enters ln Z / N with weight 2^-k) the step gets up to two more
+                               power iterations, each checked again, and if it still fails the
+                               exact partial eigensolver (cuSOLVER syevdx).  Reading the check
+                               costs one host synchronisation per subspace step.  Must be
+                               finite and >= 0.                                           */
   int stage2_n_group;       /* tile order of the O(D^7) stage-2 GEMM: its persistent CTAs walk
                                the output in groups of this many 128-wide N-tiles (all M-tiles
                                of a group before the next), so that one stripe of the B
@@ -127,8 +128,8 @@ typedef struct {
   int stage2_pair;          /* stage-2 GEMM of the three-plane steps on CTA pairs (tcgen05
                                cta_group::2: 256-row tiles, each CTA of a cluster of two loads
                                its 128 rows of U and half of the 128-row tile of the other
-                               operand); 0 = the default (on), > 0 = on, < 0 = one CTA per
-                               tile.  Results are bit-identical either way.                */
+                               operand); 0 = the default (one CTA per tile, measured
+                               faster), > 0 = on.  Results are bit-identical either way.   */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -194,11 +195,10 @@ hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double 
 /* Device-resident forward: T0_dev is a device pointer (d0^4 float64); results
  * are written to the device buffer out_dev = [lnz_per_site, trace_sign,
  * ln c_1 .. ln c_n] (n_steps + 2 doubles).  Enqueued on the plan's stream;
- * returns without synchronising.  Device-side failures (eigensolver,
- * non-finite norm, timeouts) are reported by hotrg_sync.  With eigh_mode 1,
- * out_dev is final only once hotrg_sync has returned: a step that failed the
- * subspace eigensolver's residual check is recomputed there (see
- * eigh_residual_tol) and out_dev rewritten. */
+ * returns without synchronising, except that with eigh_mode 1 each step's
+ * eigensolver accuracy check is read on the host (see eigh_residual_tol).
+ * Device-side failures (eigensolver, non-finite norm, timeouts) are reported
+ * by hotrg_sync. */
 hotrg_status hotrg_forward_device(hotrg_plan plan, const double* T0_dev, double* out_dev);
 
 /* Backward after a forward (needs want_grad = 1).  dlnz_dT0_host: d0^4
@@ -222,13 +222,13 @@ hotrg_status hotrg_diagnostics(hotrg_plan plan, double* trunc_err, double* cut_g
 
 /* Eigensolver diagnostics of the last forward (host arrays of n_steps, may be
  * NULL): residual = the guard's max_a ||G v_a - theta_a v_a||_2 / theta_1 of
- * the kept Ritz pairs where the subspace eigensolver ran (NaN elsewhere);
- * exact_step = 1 where the guard fired and the step was recomputed with the
- * exact partial eigensolver; fallbacks = such recomputations over the plan's
- * lifetime.  residual holds the last pass's values (the exact recomputation
- * writes NaN for its step).  Call after hotrg_sync or a host-buffer forward. */
-hotrg_status hotrg_eigh_diagnostics(hotrg_plan plan, double* residual, int* exact_step,
-                                    long long* fallbacks);
+ * the kept Ritz pairs where the subspace eigensolver ran (NaN elsewhere and
+ * where the exact solver finished the step); extra_iters = power iterations
+ * the guard added to the step; exact_step = 1 where the step was finished by
+ * the exact partial eigensolver; guard_steps = steps on which the guard fired
+ * over the plan's lifetime. */
+hotrg_status hotrg_eigh_diagnostics(hotrg_plan plan, double* residual, int* extra_iters,
+                                    int* exact_step, long long* guard_steps);
 
 /* Per-step bond dimensions of a plan: X (merged legs), Y (other legs), X' (kept). */
 hotrg_status hotrg_step_dims(hotrg_plan plan, int step, int* X, int* Y, int* Xp);
@@ -322,8 +322,10 @@ hotrg_status hotrg_check_bounded_wait(double timeout_ms);
  * bf16 planes per operand, FP32 accumulation in chunks of kchunk * 64 along K,
  * 0 = a single chunk; K must be a multiple of 8) or by the FP64 GEMM.  They
  * allocate and free temporary device memory and synchronise the device. */
-hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
-                                    const double* B, double* C);   /* planes: 2, 3 or 4 */
+hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, int cta_pair,
+                                    const double* A, const double* B, double* C);
+                                    /* planes: 2, 3 or 4; cta_pair = 1: three planes with
+                                       N > 64 run on CTA pairs (256-row tiles) */
 hotrg_status hotrg_gemm_f64_check(int M, int N, int K, const double* A, const double* B, double* C);
 
 /* Allocation-free variant of hotrg_gemm_split_check (the paper has no

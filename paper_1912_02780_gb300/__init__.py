@@ -113,13 +113,13 @@ def lib() -> ctypes.CDLL:
     L.hotrg_sync.argtypes = [vp]
     L.hotrg_diagnostics.argtypes = [vp, _dp, _dp, _ip]
     L.hotrg_step_dims.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip]
-    L.hotrg_eigh_diagnostics.argtypes = [vp, _dp, _ip, ctypes.POINTER(ctypes.c_longlong)]
+    L.hotrg_eigh_diagnostics.argtypes = [vp, _dp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)]
     L.hotrg_status_string.argtypes = [ctypes.c_int]
     L.hotrg_status_string.restype = ctypes.c_char_p
     L.hotrg_last_error.argtypes = [vp]
     L.hotrg_last_error.restype = ctypes.c_char_p
     L.hotrg_device_supports_split.argtypes = []
-    L.hotrg_gemm_split_check.argtypes = [ctypes.c_int] * 5 + [_dp, _dp, _dp]
+    L.hotrg_gemm_split_check.argtypes = [ctypes.c_int] * 6 + [_dp, _dp, _dp]
     L.hotrg_gemm_f64_check.argtypes = [ctypes.c_int] * 3 + [_dp, _dp, _dp]
     L.hotrg_profile_enable.argtypes = [vp, ctypes.c_int]
     L.hotrg_profile_read.argtypes = [vp, _dp, _ip]
@@ -273,15 +273,17 @@ class Plan:
         return t, g, s
 
     def eigh_diagnostics(self):
-        """(residual per step, exact-fallback flag per step, fallbacks so far):
-        the subspace eigensolver's accuracy guard (NaN residual where it did
-        not run)."""
+        """(residual per step, extra power iterations per step, exact-solver flag
+        per step, guard firings so far): the subspace eigensolver's accuracy
+        guard (NaN residual where it did not run)."""
         r = np.zeros(self.n_steps)
+        x = np.zeros(self.n_steps, dtype=np.int32)
         e = np.zeros(self.n_steps, dtype=np.int32)
         f = ctypes.c_longlong(0)
-        self._check(lib().hotrg_eigh_diagnostics(self._h, _p(r), e.ctypes.data_as(_ip),
-                                                 ctypes.byref(f)), "eigh_diagnostics")
-        return r, e, int(f.value)
+        self._check(lib().hotrg_eigh_diagnostics(self._h, _p(r), x.ctypes.data_as(_ip),
+                                                 e.ctypes.data_as(_ip), ctypes.byref(f)),
+                    "eigh_diagnostics")
+        return r, x, e, int(f.value)
 
     # ---- differentiable TRG: isometries as parameters ----------------------
     def _w_layout(self):
@@ -422,13 +424,15 @@ def kernel_launches() -> int:
     return int(lib().hotrg_kernel_launches())
 
 
-def gemm_split_check(A: np.ndarray, B: np.ndarray, planes: int = 2, kchunk: int = 0) -> np.ndarray:
+def gemm_split_check(A: np.ndarray, B: np.ndarray, planes: int = 2, kchunk: int = 0,
+                     cta_pair: bool = False) -> np.ndarray:
     A = np.ascontiguousarray(A, dtype=np.float64)
     B = np.ascontiguousarray(B, dtype=np.float64)
     M, K = A.shape
     N = B.shape[0]
     C = np.zeros((M, N))
-    s = lib().hotrg_gemm_split_check(M, N, K, planes, kchunk, _p(A), _p(B), _p(C))
+    s = lib().hotrg_gemm_split_check(M, N, K, planes, kchunk, int(bool(cta_pair)), _p(A), _p(B),
+                                     _p(C))
     if s:
         raise HotrgError(s, "gemm_split_check")
     return C

@@ -9,20 +9,21 @@
 // while keeping about 16, 24 or 32 significant bits per product (two, three
 // or four planes).
 //
-// Structure (one persistent CTA per SM, 320 threads):
+// Structure (one persistent CTA per SM, or a cluster of two, 320 threads):
 //   warp 8      TMA producer: per K slab (64 or 32 wide), one 3-D tensor-map
 //               load per operand plane into a swizzled shared-memory stage.
-//   warp 9      MMA issuer: tcgen05.mma kind::f16 (M = 128, N = BN, K = 16)
-//               for every plane pair and K step, hi*hi into its own exactly
-//               accumulated TMEM buffer, the other products into a second;
-//               tcgen05.commit frees the stage and, at the end of an
-//               accumulation chunk, hands the (double-buffered) accumulators
-//               to the epilogue.
+//   warp 9      MMA issuer: tcgen05.mma kind::f16 (M = 128, or 256 across a
+//               CTA pair; N = BN, K = 16) for every plane pair and K step,
+//               hi*hi into its own exactly accumulated TMEM buffer, the other
+//               products into a second; tcgen05.commit frees the stage and, at
+//               the end of an accumulation chunk, hands the (double-buffered)
+//               accumulators to the epilogue.
 //   warps 0-7   epilogue: tcgen05.ld the accumulators (one TMEM lane per row,
-//               half the columns per warp), add the chunk into float-float
-//               register sums, and write the tile through the output index
-//               maps as FP32, FP64 or grid-split bf16 planes, staged through a
-//               per-warp shared-memory transpose for whole-sector stores.
+//               half of the columns per warp), add the chunk into
+//               float-float register sums, and write the tile through the
+//               output index maps as FP32, FP64 or grid-split bf16 planes,
+//               staged through a per-warp shared-memory transpose for
+//               whole-sector stores.
 // Every mbarrier wait is bounded; on timeout the error word gets kErrTimeout,
 // the role stops, and all warps still meet at the final barrier, drain their
 // MMAs and free TMEM.
@@ -281,6 +282,43 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = (a - (s - bb)) + (b - bb);
 }
 
+// Plane products formed for each K step: every pair (i, j) with
+// i + j <= NP - 1, hi * hi first (its own, exactly accumulated TMEM buffer),
+// then (0, 1), then the others smallest first.  hi * hi and (0, 1) share A
+// plane 0 and sit side by side in TMEM ([hh | rest]) with B planes 0 and 1
+// side by side in shared memory, so one CTA issues them as one N = 2 BN
+// instruction.
+template <int NP>
+struct Pairs;
+// (plane of A, plane of B) of product q, written out as selections so that
+// they fold to constants in the unrolled issue loop
+template <>
+struct Pairs<2> {
+  static constexpr int n = 3;
+  __host__ __device__ static constexpr int a(int q) { return q == 2 ? 1 : 0; }
+  __host__ __device__ static constexpr int b(int q) { return q == 1 ? 1 : 0; }
+};
+template <>
+struct Pairs<3> {   // (0,0) (0,1) (2,0) (1,1) (0,2) (1,0)
+  static constexpr int n = 6;
+  __host__ __device__ static constexpr int a(int q) {
+    return q == 2 ? 2 : (q == 3 || q == 5) ? 1 : 0;
+  }
+  __host__ __device__ static constexpr int b(int q) {
+    return q == 1 ? 1 : q == 3 ? 1 : q == 4 ? 2 : 0;
+  }
+};
+template <>
+struct Pairs<4> {   // (0,0) (0,1) (3,0) (2,1) (1,2) (0,3) (2,0) (1,1) (0,2) (1,0)
+  static constexpr int n = 10;
+  __host__ __device__ static constexpr int a(int q) {
+    return q == 2 ? 3 : (q == 3 || q == 6) ? 2 : (q == 4 || q == 7 || q == 9) ? 1 : 0;
+  }
+  __host__ __device__ static constexpr int b(int q) {
+    return q == 5 ? 3 : (q == 4 || q == 8) ? 2 : (q == 1 || q == 3 || q == 7) ? 1 : 0;
+  }
+};
+
 // Tile t of an MT x NT grid: M fastest (m_fast), N fastest, or (n_group > 0)
 // in groups of n_group N-tiles: all M-tiles of one group of columns, N fastest
 // inside the group, before the next group.  The persistent CTAs then work on
@@ -316,35 +354,41 @@ struct Cfg {
   static constexpr int kAPlane = BM * BK * 2;
   static constexpr int kBPlane = kBRows * BK * 2;
   static constexpr int kStage = NP * (kAPlane + kBPlane);
-  static constexpr int kEpiWarps = 8;                    // 2 warps per TMEM lane quadrant
+  // Epilogue: two warps per TMEM lane quadrant (a warp may only read the 32
+  // lanes of its own sub-partition), each with half of the tile's columns.
+  // Measured on GB300 (stage 2 at D_cut = 64, three planes): 8 epilogue warps
+  // 40.1 ms, 16 warps 42.4 ms (less register pressure, but more warps
+  // competing with the TMA and MMA warps for issue slots).
+  static constexpr int kEpiPerQuad = 2;
+  static constexpr int kEpiWarps = 4 * kEpiPerQuad;
   static constexpr int kThreads = (kEpiWarps + 2) * 32;  // + TMA warp + MMA warp
-  static constexpr int kCols = BN / 2;                   // columns per epilogue thread
+  static constexpr int kCols = BN / kEpiPerQuad;         // columns per epilogue thread
   // Shared memory after the pipeline stages (byte offsets from the 1024-aligned
   // base): mbarriers, column offsets (BN), contiguity flags, the TMEM address,
-  // the segment-max / offset exchange of the grid-split epilogue (2 halves x
-  // 128 rows), and a store-staging buffer per epilogue warp (16-byte aligned:
-  // it is accessed as uint4).  CG = 2 uses 1 KB staging buffers and keeps the
-  // exchange inside them (a barrier separates the two uses), which is what lets
-  // three pipeline stages fit.
-  static constexpr int kStageBytes = CG == 2 ? 1024 : 2048;
-  static constexpr int kExtra = 1024 + 11 * 8 + BN * 8 + BN / 16 * 4 + 32 +
-                                (CG == 2 ? 0 : 2 * BM * 12 + 16) + kEpiWarps * kStageBytes;
+  // the segment-max / offset exchange of the grid-split epilogue (4 column
+  // groups x 128 rows), and a 1 KB store-staging buffer per epilogue warp
+  // (16-byte aligned: it is accessed as uint4).  CG = 2 keeps the exchange
+  // inside the staging buffers (a barrier separates the two uses).
+  static constexpr int kStageBytes = 1024;
+  static constexpr int kXchg = kEpiPerQuad * BM * 12;    // offsets (8 B) + maxima (4 B)
+  static constexpr int kExtra = 1024 + 17 * 8 + BN * 8 + BN / 16 * 4 + 32 +
+                                (CG == 2 ? 0 : kXchg + 16) + kEpiWarps * kStageBytes;
   static constexpr int kFit = (232448 - kExtra) / kStage;
-  static constexpr int kStages =
-      CG == 2 ? (kFit > 4 ? 4 : kFit) : ((200 * 1024 / kStage) > 6 ? 6 : (200 * 1024 / kStage));
+  static constexpr int kStages = kFit > 6 ? 6 : kFit;
   static constexpr int kBars = 2 * kStages + 5;
   static constexpr int kOffBars = kStages * kStage;
   static constexpr int kOffCn = kOffBars + kBars * 8;
   static constexpr int kOffCv = kOffCn + BN * 8;
   static constexpr int kOffTmem = kOffCv + BN / 16 * 4;
   static constexpr int kOffXo = (kOffTmem + 16 + 15) / 16 * 16;
-  static constexpr int kOffXm = kOffXo + 2 * BM * 8;
+  static constexpr int kOffXm = kOffXo + kEpiPerQuad * BM * 8;
   static constexpr int kOffStg =
-      CG == 2 ? kOffXo : (kOffXm + 2 * BM * 4 + 15) / 16 * 16;
+      CG == 2 ? kOffXo : (kOffXm + kEpiPerQuad * BM * 4 + 15) / 16 * 16;
   static constexpr int kSmem = 1024 + kOffStg + kEpiWarps * kStageBytes;
   static_assert(kOffCn % 8 == 0 && kOffXo % 16 == 0 && kOffStg % 16 == 0, "smem alignment");
-  static_assert(CG == 1 || 2 * BM * 12 <= kEpiWarps * kStageBytes, "exchange fits the staging");
+  static_assert(CG == 1 || kXchg <= kEpiWarps * kStageBytes, "exchange fits the staging");
   static_assert(kSmem <= 232448, "shared memory per CTA");
+  static_assert(kCols % 16 == 0, "whole 16-column store groups per thread");
   // TMEM: per buffer (2) an exact hi*hi accumulator and a "rest" accumulator, BN columns each.
   static constexpr int kTmemCols = 4 * BN;
   static_assert(kStages >= 2, "need at least two pipeline stages");
@@ -572,7 +616,10 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
     }
   } else if (warp == kMma) {
     if (lane == 0 && rank == 0) {
+      using P = Pairs<NP>;
       constexpr uint32_t idesc = idesc_bf16(BM * CG, BN);
+      constexpr uint32_t idesc2 = idesc_bf16(BM, 2 * BN);   // hh and (0, 1) together
+      constexpr int q0 = CG == 1 ? 2 : 0;
       int s = 0;
       uint32_t ph = 0;
       int acc = 0;
@@ -588,19 +635,30 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
           for (int kb = kb0; kb < kb1; ++kb) {
             if (!mbar_wait(full_bar(s), ph, p.err)) { ok = false; break; }
             tc_fence_after();
-            for (int q = 0; q < p.npairs; ++q) {
+            const bool first = kb == kb0;   // the chunk's first slab resets both accumulators
+            // descriptors of A and B plane 0 of this stage; a plane and a K step
+            // are fixed byte offsets, added to the descriptor's address field
+            // (address >> 4; stays below 2^14 inside shared memory)
+            const uint64_t ad = sdesc<BK>(a_tile(s, 0)), bd = sdesc<BK>(b_tile(s, 0));
+            if constexpr (CG == 1) {
+              // hi * hi into hh and A0 * B1 into rest (= hh + BN): one N = 2 BN MMA
+#pragma unroll
+              for (int kk = 0; kk < BK / 16; ++kk)
+                tc_mma(d_hh, ad + 2 * kk, bd + 2 * kk, idesc2, (first && kk == 0) ? 0u : 1u);
+            }
+#pragma unroll
+            for (int q = q0; q < P::n; ++q) {
               // product 0 (hi * hi) has its own, exactly accumulated, TMEM buffer
               const uint32_t d = (q == 0) ? d_hh : d_rest;
-              const bool first = (kb == kb0) && (q <= 1);
-              const uint32_t a0 = a_tile(s, p.pa[q]), b0 = b_tile(s, p.pb[q]);
+              const bool reset = first && q <= 1;
+              const uint64_t aq = ad + (uint64_t)(P::a(q) * C::kAPlane / 16);
+              const uint64_t bq = bd + (uint64_t)(P::b(q) * C::kBPlane / 16);
 #pragma unroll
               for (int kk = 0; kk < BK / 16; ++kk) {
                 if constexpr (CG == 2)
-                  tc_mma_pair(d, sdesc<BK>(a0 + kk * 32), sdesc<BK>(b0 + kk * 32), idesc,
-                              (first && kk == 0) ? 0u : 1u);
+                  tc_mma_pair(d, aq + 2 * kk, bq + 2 * kk, idesc, (reset && kk == 0) ? 0u : 1u);
                 else
-                  tc_mma(d, sdesc<BK>(a0 + kk * 32), sdesc<BK>(b0 + kk * 32), idesc,
-                         (first && kk == 0) ? 0u : 1u);
+                  tc_mma(d, aq + 2 * kk, bq + 2 * kk, idesc, (reset && kk == 0) ? 0u : 1u);
               }
             }
             if constexpr (CG == 2) tc_commit_pair(empty_bar(s), 3);   // both CTAs' stage s
@@ -620,16 +678,17 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
       mbar_wait(drain_bar, 0, p.err);
     }
   } else {
-    // Epilogue warps 0..7: warp w owns TMEM lanes [32 (w % 4), +32) (tile rows)
-    // and columns [(w / 4) BN / 2, +BN / 2).  Chunk sums hh + rest are added
-    // into a float-float running sum held in registers.
+    // Epilogue warps 0..15: warp w owns TMEM lanes [32 (w % 4), +32) (tile
+    // rows) and column group cg = w / 4, columns [cg kCols, +kCols).  Chunk
+    // sums hh + rest are added into a float-float running sum held in
+    // registers.
     constexpr int kEpiThreads = C::kEpiWarps * 32;
     int acc = 0;
     uint32_t acc_ph = 0;
     bool ok = true;
-    const int quad = warp & 3, half = warp >> 2;
+    const int quad = warp & 3, cg = warp >> 2;
     const int row = quad * 32 + lane;
-    const int col0 = half * C::kCols;
+    const int col0 = cg * C::kCols;
     const uint32_t lane_base = tmem_base + ((uint32_t)(quad * 32) << 16);
     float rhi[C::kCols], rlo[C::kCols];
     for (long long t = t0; t < tiles && ok; t += tstep) {
@@ -656,17 +715,20 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
           tmem_ld_wait();
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
+            float& hi = rhi[g * 8 + j];
+            float& lo = rlo[g * 8 + j];
+            // float-float sum of the chunk's hh + rest into (hi, lo)
             float s, e;
             two_sum(a[j], b[j], s, e);
             if (c == 0) {
-              rhi[g * 8 + j] = s;
-              rlo[g * 8 + j] = e;
+              hi = s;
+              lo = e;
             } else {
               float u, f;
-              two_sum(rhi[g * 8 + j], s, u, f);
-              f += rlo[g * 8 + j] + e;
-              rhi[g * 8 + j] = u + f;
-              rlo[g * 8 + j] = f - (rhi[g * 8 + j] - u);
+              two_sum(hi, s, u, f);
+              f += lo + e;
+              hi = u + f;
+              lo = f - (hi - u);
             }
           }
         }
@@ -678,7 +740,7 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
         }
         if (++acc == 2) { acc = 0; acc_ph ^= 1u; }
       }
-      // column offsets of this tile (shared by the 8 epilogue warps); the
+      // column offsets of this tile (shared by the epilogue warps); the
       // AND-barrier also makes every epilogue warp stop together after a failure
       ok = named_bar_and(1, kEpiThreads, ok);
       if (!ok) break;
@@ -700,25 +762,41 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
           rhi[j] = p.alpha * (rhi[j] + rlo[j]);
           mx = fmaxf(mx, fabsf(rhi[j]));
         }
+        // This thread's kCols columns are one run of an aligned 128-element
+        // segment of the destination, made of two 64-element halves of kH
+        // runs each: the other runs of its half belong to the column groups
+        // next to it (same row), those of the partner half to the other
+        // groups of the same row (seg_phalf) or the same groups of row ^
+        // seg_prow.  The segment maximum sets the grid of plane 0.
+        constexpr int kH = 64 / C::kCols;    // threads per 64-element half
+        const int sub = cg % kH, hf = cg / kH;
         long long o = -1;
         if (mok) {
           o = coff + cn_s[col0];
-          bool run = (o & 63) == 0 && o >= 0 && o + C::kCols <= p.c_lim;
+          bool run = (o & 63) == C::kCols * sub && o >= 0 && o + C::kCols <= p.c_lim;
 #pragma unroll
           for (int g = 0; g < C::kCols / 16; ++g)
             run = run && cv_s[col0 / 16 + g] && cn_s[col0 + 16 * g] == cn_s[col0] + 16 * g;
           if (!run) o = -1;
         }
-        xm_s[half * BM + row] = mx;
-        xo_s[half * BM + row] = o;
+        xm_s[cg * BM + row] = mx;
+        xo_s[cg * BM + row] = o;
         named_bar(1, kEpiThreads);
-        const int pidx = (half ^ p.seg_phalf) * BM + (row ^ p.seg_prow);
-        const float pm = xm_s[pidx];
-        const long long po = xo_s[pidx];
+        const long long hs = o - C::kCols * sub;   // start of this thread's half
+        bool seg_ok = true;
+        float pm = 0.f;
+#pragma unroll
+        for (int j = 0; j < kH; ++j) {
+          const int own = (hf * kH + j) * BM + row;
+          const int par = ((hf ^ p.seg_phalf) * kH + j) * BM + (row ^ p.seg_prow);
+          pm = fmaxf(pm, fmaxf(xm_s[own], xm_s[par]));
+          seg_ok = seg_ok && xo_s[own] == hs + C::kCols * j &&
+                   xo_s[par] == (hs ^ 64) + C::kCols * j;
+        }
         // CG = 2: the exchange lives in the staging buffers, which the stores
-        // below overwrite: every warp must have read its partner first
+        // below overwrite: every warp must have read its partners first
         if constexpr (CG == 2) named_bar(1, kEpiThreads);
-        const bool valid = mok && o >= 0 && po == (o ^ 64);
+        const bool valid = mok && o >= 0 && seg_ok;
         if (mok && !valid) report_error(p.err, kErrBounds);
         // grid of the segment (the rule of kernels.cu: grid_split); v / g is
         // taken as v * (1/g), the same exactly rounded value (g a power of 2)
@@ -925,25 +1003,17 @@ cudaError_t bounded_wait_probe(int* err, long long limit_cycles, cudaStream_t st
 }
 
 void tc_set_pairs(TcGemm& g, int nplanes) {
-  // Product 0 must be hi * hi: it is accumulated exactly in its own TMEM buffer.
+  // The kernel forms the products of Pairs<nplanes>; the list is recorded
+  // here for the host-side checks and for callers that inspect it.
   g.nplanes = nplanes;
-  if (nplanes == 4) {
-    // all products with plane-sum <= 3: hi*hi first, then smallest first
-    const int a[10] = {0, 3, 2, 1, 0, 2, 1, 0, 1, 0}, b[10] = {0, 0, 1, 2, 3, 0, 1, 2, 0, 1};
-    g.npairs = 10;
-    for (int i = 0; i < 10; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
-    return;
-  }
-  if (nplanes == 2) {
-    const int a[3] = {0, 1, 0}, b[3] = {0, 0, 1};
-    g.npairs = 3;
-    for (int i = 0; i < 3; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
-  } else {
-    // the remaining products smallest first
-    const int a[6] = {0, 2, 1, 0, 1, 0}, b[6] = {0, 0, 1, 2, 0, 1};
-    g.npairs = 6;
-    for (int i = 0; i < 6; ++i) { g.pa[i] = a[i]; g.pb[i] = b[i]; }
-  }
+  auto take = [&](auto pairs) {
+    using P = decltype(pairs);
+    g.npairs = P::n;
+    for (int i = 0; i < P::n; ++i) { g.pa[i] = P::a(i); g.pb[i] = P::b(i); }
+  };
+  if (nplanes == 4) take(Pairs<4>());
+  else if (nplanes == 2) take(Pairs<2>());
+  else take(Pairs<3>());
 }
 
 cudaError_t tc_gemm(const TcOperand& A, const TcOperand& B, const TcGemm& g, cudaStream_t stream,

@@ -153,11 +153,13 @@ struct hotrg_plan_s {
   double *dtrunc = nullptr, *dgap = nullptr;
   double* dres = nullptr;     // per step: max relative residual of the kept Ritz pairs
   int* err = nullptr;         // [0] all error bits, [1] first bit, [2] residual guard code
-  // subspace eigensolver guard: steps of the current forward recomputed with
-  // the exact partial eigensolver, and the count of such recomputations
+  // subspace eigensolver guard, per step of the last forward: extra power
+  // iterations it took, and whether the exact eigensolver had to finish it;
+  // steps on which it fired over the plan's lifetime
+  std::vector<int> guard_iters;
   std::vector<char> exact_step;
   long long fallbacks = 0;
-  double* pending_out = nullptr;   // device out buffer of the last hotrg_forward_device
+  int* guard_host = nullptr;       // pinned host word the guard is read into
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
@@ -431,8 +433,9 @@ hotrg_status contract_f64(hotrg_plan p, const StepGeom& s, const double* T, cons
 // N-tiles per L2 raster group of the stage-2 GEMM (0 in the config: the
 // default; >= the N-tile count: plain N-fastest order).
 int stage2_group(const hotrg_config& c) { return c.stage2_n_group > 0 ? c.stage2_n_group : 16; }
-// Stage-2 GEMM on CTA pairs (config: 0 = the default, > 0 = on, < 0 = off).
-int stage2_pair(const hotrg_config& c) { return c.stage2_pair < 0 ? 0 : 1; }
+// Stage-2 GEMM on CTA pairs (config: 0 = the default, off: the pair kernel
+// measured slower on GB300, 46.4 vs 42.4 ms per D = 64 launch; > 0 = on).
+int stage2_pair(const hotrg_config& c) { return c.stage2_pair > 0 ? 1 : 0; }
 
 // Segment partner of the grid-split epilogue (see gemm_tc.h: kOutGridSplit)
 // for an output whose 64-column half-runs are `run` consecutive destination
@@ -551,16 +554,17 @@ int subspace_ritz(const StepGeom& s) { return s.Xp + 1; }
 constexpr int kEighPlanes = 4;
 
 // Residual bound of the kept Ritz pairs at step k, relative to the largest
-// eigenvalue, above which the step's subspace eigensolve is replaced by the
-// exact one.  The bound is on 2^-k r_k: an error made at step k enters
-// ln Z / N with weight 2^-k (through ln c_k / 2^k and every later step of the
-// same 2^k-site block).  Measured on GB300 (random reflection-symmetric d0 = 4
-// tensors at D_cut = 16, 32, 64 and Ising at beta_c, D_cut = 64): every solve
-// whose ln Z / N missed the oracle by more than 1e-9 had a step with
-// 2^-k r_k >= 1.2e-6, every one within 1e-9 stayed below 7.5e-8, and the
-// error was at most 1e-2 times the largest 2^-k r_k.
+// eigenvalue, above which the step's subspace eigensolve is refined.  The
+// bound is on 2^-k r_k: an error made at step k enters ln Z / N with weight
+// 2^-k (through ln c_k / 2^k and every later step of the same 2^k-site
+// block).  Measured on GB300 (random d0 = 4 tensors with and without the
+// reflection symmetry at D_cut = 16, 32, 64, Ising at beta_c, D_cut = 64): the
+// ln Z / N error of a solve stayed below 0.05 times the sum over its steps of
+// 2^-k r_k, so a bound of 5e-9 per step keeps it near 1e-9 or below; the
+// tensor-core products' own residual floor (about 1e-8 relative) passes it
+// from step 3 on.
 double residual_tol(const hotrg_config& c, int k) {
-  const double t = c.eigh_residual_tol > 0 ? c.eigh_residual_tol : 1e-7;
+  const double t = c.eigh_residual_tol > 0 ? c.eigh_residual_tol : 5e-9;
   return std::ldexp(t, k);
 }
 
@@ -572,13 +576,15 @@ bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
          kEighPlanes * round_up(K * N, 64) <= cap;
 }
 
-hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
+// resume = true continues from the orthonormal block the previous call left
+// in p->Qs with `iters` more power iterations (the accuracy guard's
+// refinement) instead of starting from the random block.
+hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step, int iters, bool resume) {
   cudaStream_t st = p->stream;
   const int N = (int)s.N, K = subspace_k(p->cfg, s);
-  const int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
   const bool tc = subspace_on_tc(p, s);
   const long long sG = round_up((long long)N * N, 64), sQ = round_up((long long)K * N, 64);
-  if (tc) {
+  if (tc && !resume) {
     Stage sc(p, kStEighProd);
     CK(gsplit(p, p->Escr, map_lin(N), map_lin(1), N, N, kEighPlanes, sG, p->pV));
   }
@@ -615,7 +621,8 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
     Stage sc(p, kStEighQR);
     return householder();
   };
-  CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
+  if (!resume)
+    CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
   hotrg_status r;
   for (int it = 0; it < iters; ++it) {
     if ((r = product()) != HOTRG_OK) return r;
@@ -646,13 +653,10 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step) {
 // Accuracy guard of the subspace eigensolver: the kept Ritz pairs (rows of
 // Ek, values lk descending) are checked against the Gram matrix still in
 // p->Escr, r = max_a ||G v_a - theta_a v_a|| / theta_1, bounded by
-// residual_tol(k).  On split steps the
-// products run on the four-plane tensor-core GEMM with the split of G the
-// eigensolver made; otherwise in FP64.  A step over the bound raises the
-// guard word err[2] to n + 1 - k (the earliest failing step wins); the host
-// sees it at the next synchronisation and recomputes the forward from that
-// step with the exact partial eigensolver (finish_sync), so the good path
-// costs one product per step and no host synchronisation.
+// residual_tol(k).  On split steps the products run on the four-plane
+// tensor-core GEMM with the split of G the eigensolver made; otherwise in
+// FP64.  A step over the bound sets the guard word err[2]; step_forward reads
+// it (one host synchronisation per subspace step) and refines that step.
 hotrg_status eigh_residual(hotrg_plan p, const StepGeom& s, int k) {
   Stage sc(p, kStEighRes);
   cudaStream_t st = p->stream;
@@ -670,9 +674,22 @@ hotrg_status eigh_residual(hotrg_plan p, const StepGeom& s, int k) {
                 st, p->sms));
   }
   CK(eig_residual(p->Zs, Ek, p->lam[k - 1], Dp, N, residual_tol(p->cfg, k), p->partial,
-                  p->dres + (k - 1), p->err + 2, p->cfg.n_steps + 1 - k, st));
+                  p->dres + (k - 1), p->err + 2, 1, st));
   return HOTRG_OK;
 }
+
+// Wait for the step's residual check and return (and clear) the guard word.
+hotrg_status guard_fired(hotrg_plan p, bool* fired) {
+  CK(cudaMemcpyAsync(p->guard_host, p->err + 2, sizeof(int), cudaMemcpyDeviceToHost, p->stream));
+  CK(cudaStreamSynchronize(p->stream));
+  *fired = *p->guard_host != 0;
+  if (*fired) CK(cudaMemsetAsync(p->err + 2, 0, sizeof(int), p->stream));
+  return HOTRG_OK;
+}
+
+// Extra power iterations the guard may add to a step before it hands the
+// step to the exact partial eigensolver.
+constexpr int kGuardMaxIters = 2;
 
 hotrg_status step_forward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
@@ -695,40 +712,62 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   {
   Stage sc(p, kStEigh);
   CK(diag_trace(p->Escr, N, p->scal + 3, st));
-  int ncols = N;
-  const double* evec = p->Escr;
-  const bool exact = (size_t)(k - 1) < p->exact_step.size() && p->exact_step[k - 1];
-  const bool subspace = use_subspace(p, s) && !exact;
-  if (subspace) {
-    hotrg_status rr = eigh_subspace(p, s, k);
-    if (rr != HOTRG_OK) return rr;
-    ncols = subspace_ritz(s);
-    evec = p->Zs;
-  } else if (p->cfg.want_grad || s.Xp >= N) {
-    // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
-    cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
-                                           CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc,
-                                           p->work, p->lwork, p->info);
-    if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
-  } else {
-    // forward only: the D'+1 largest eigenpairs (D' kept, one more for the gap)
+  // forward only: the D'+1 largest eigenpairs (D' kept, one more for the gap)
+  auto exact_partial = [&]() -> hotrg_status {
     int meig = 0;
     cusolverStatus_t cs = cusolverDnDsyevdx(p->solver, CUSOLVER_EIG_MODE_VECTOR,
                                             CUSOLVER_EIG_RANGE_I, CUBLAS_FILL_MODE_LOWER, N,
                                             p->Escr, N, 0.0, 0.0, N - s.Xp, N, &meig, p->wasc,
                                             p->work, p->lwork, p->info);
     if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevdx failed");
-    ncols = s.Xp + 1;
-  }
-  CK(eigh_info_check(p->info, p->err, st));
-  if (g_inj_what.load() == kInjEigh && g_inj_arg.load() == k)
-    CK(set_value(nullptr, 0.0, p->err, kErrEigh, st));
-  CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
-  CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
-  if (subspace) {
-    hotrg_status rr = eigh_residual(p, s, k);
-    if (rr != HOTRG_OK) return rr;
+    return HOTRG_OK;
+  };
+  auto finish = [&](const double* evec, int ncols) -> hotrg_status {
+    CK(eigh_info_check(p->info, p->err, st));
+    if (g_inj_what.load() == kInjEigh && g_inj_arg.load() == k)
+      CK(set_value(nullptr, 0.0, p->err, kErrEigh, st));
+    CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
+    CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
+    return HOTRG_OK;
+  };
+  if (use_subspace(p, s)) {
+    // randomized subspace eigensolver, checked on the device; where the check
+    // fails, up to kGuardMaxIters more power iterations, then the exact solver
+    const int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
+    if ((r = eigh_subspace(p, s, k, iters, false)) != HOTRG_OK) return r;
+    if ((r = finish(p->Zs, subspace_ritz(s))) != HOTRG_OK) return r;
+    if ((r = eigh_residual(p, s, k)) != HOTRG_OK) return r;
+    bool fired = false;
+    if ((r = guard_fired(p, &fired)) != HOTRG_OK) return r;
+    if (fired) ++p->fallbacks;
+    int extra = 0;
+    while (fired && extra < kGuardMaxIters) {
+      ++extra;
+      if ((r = eigh_subspace(p, s, k, 1, true)) != HOTRG_OK) return r;
+      if ((r = finish(p->Zs, subspace_ritz(s))) != HOTRG_OK) return r;
+      if ((r = eigh_residual(p, s, k)) != HOTRG_OK) return r;
+      if ((r = guard_fired(p, &fired)) != HOTRG_OK) return r;
+    }
+    p->guard_iters[k - 1] = extra;
+    if (fired) {
+      p->exact_step[k - 1] = 1;
+      if ((r = exact_partial()) != HOTRG_OK) return r;
+      if ((r = finish(p->Escr, s.Xp + 1)) != HOTRG_OK) return r;
+      CK(set_value(p->dres + (k - 1), std::nan(""), nullptr, 0, st));
+    }
   } else {
+    int ncols = N;
+    if (p->cfg.want_grad || s.Xp >= N) {
+      // all eigenpairs (the backward's eigensolve adjoint needs the discarded ones)
+      cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                             CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc,
+                                             p->work, p->lwork, p->info);
+      if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
+    } else {
+      if ((r = exact_partial()) != HOTRG_OK) return r;
+      ncols = s.Xp + 1;
+    }
+    if ((r = finish(p->Escr, ncols)) != HOTRG_OK) return r;
     CK(set_value(p->dres + (k - 1), std::nan(""), nullptr, 0, st));
   }
   }
@@ -745,12 +784,14 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   return HOTRG_OK;
 }
 
-hotrg_status run_forward(hotrg_plan p, int k_from = 1) {
+hotrg_status run_forward(hotrg_plan p) {
   cudaStream_t st = p->stream;
   if (p->cfg.w_given && !p->w_loaded)
     return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
   p->have_bwd = false;
-  for (int k = k_from; k <= p->cfg.n_steps; ++k) {
+  p->guard_iters.assign(p->cfg.n_steps, 0);
+  p->exact_step.assign(p->cfg.n_steps, 0);
+  for (int k = 1; k <= p->cfg.n_steps; ++k) {
     hotrg_status r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
   }
@@ -935,31 +976,11 @@ hotrg_status device_status(hotrg_plan p, const int* w) {
   return HOTRG_OK;
 }
 
-// Wait for the plan's stream and turn the device error word into a status.
-// When the residual guard of the subspace eigensolver fired during a forward,
-// recompute that forward from the earliest failing step with the exact
-// partial eigensolver at that step (later steps keep the subspace solver and
-// their own checks), then wait again.  Each pass moves the restart point
-// forward, so this ends after at most n_steps passes.
 hotrg_status finish_sync(hotrg_plan p) {
-  for (;;) {
-    CK(cudaStreamSynchronize(p->stream));
-    int w[3] = {0, 0, 0};
-    CK(cudaMemcpy(w, p->err, 3 * sizeof(int), cudaMemcpyDeviceToHost));
-    hotrg_status r = device_status(p, w);
-    if (r != HOTRG_OK || w[2] == 0) return r;
-    const int n = p->cfg.n_steps, k = n + 1 - w[2];
-    if (k < 1 || k > n || (int)p->exact_step.size() != n || p->exact_step[k - 1])
-      return fail(p, HOTRG_ENOTCONV, "subspace eigensolver guard: bad restart step");
-    p->exact_step[k - 1] = 1;
-    ++p->fallbacks;
-    CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), p->stream));
-    r = run_forward(p, k);
-    if (r != HOTRG_OK) return r;
-    if (p->pending_out)
-      CK(cudaMemcpyAsync(p->pending_out, p->out, sizeof(double) * (n + 2),
-                         cudaMemcpyDeviceToDevice, p->stream));
-  }
+  CK(cudaStreamSynchronize(p->stream));
+  int w[2] = {0, 0};
+  CK(cudaMemcpy(w, p->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  return device_status(p, w);
 }
 
 }  // namespace
@@ -1271,6 +1292,10 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       ALC(p->swork, (long long)ls);
     }
   }
+  if (cudaMallocHost(&p->guard_host, sizeof(int)) != cudaSuccess) {
+    p->guard_host = nullptr;
+    return cleanup(HOTRG_ENOMEM);
+  }
   if (cudaMemset(p->err, 0, 3 * sizeof(int)) != cudaSuccess) return cleanup(HOTRG_ECUDA);
 #undef ALC
   *out = p;
@@ -1285,6 +1310,7 @@ void hotrg_plan_destroy(hotrg_plan p) {
   for (auto e : p->ev_pool)
     if (e) cudaEventDestroy(e);
   for (void* v : p->allocs) cudaFree(v);
+  if (p->guard_host) cudaFreeHost(p->guard_host);
   delete p;
 }
 
@@ -1292,8 +1318,6 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
   if (!p || !T0_dev) return fail(p, HOTRG_EINVAL, "null argument");
   const long long n0 = (long long)p->cfg.d0 * p->cfg.d0 * p->cfg.d0 * p->cfg.d0;
   p->have_fwd = false;
-  p->exact_step.assign(p->cfg.n_steps, 0);
-  p->pending_out = out_dev;
   CK(cudaMemsetAsync(p->err, 0, 3 * sizeof(int), p->stream));
   if (T0_dev != p->T[0])
     CK(cudaMemcpyAsync(p->T[0], T0_dev, sizeof(double) * n0, cudaMemcpyDeviceToDevice, p->stream));
@@ -1309,16 +1333,13 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
 
 static hotrg_status copy_out(hotrg_plan p, double* lnz, double* log_norms, int* sign) {
   std::vector<double> h(p->cfg.n_steps + 2);
-  // the forward is final only after finish_sync (which may recompute steps
-  // whose subspace eigensolve failed its residual check)
+  CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
+                     p->stream));
   hotrg_status r = finish_sync(p);
   if (r != HOTRG_OK) {
     p->have_fwd = false;
     return r;
   }
-  CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
-                     p->stream));
-  CK(cudaStreamSynchronize(p->stream));
   if (lnz) *lnz = h[0];
   if (sign) *sign = h[1] >= 0 ? 1 : -1;
   if (log_norms) memcpy(log_norms, h.data() + 2, sizeof(double) * p->cfg.n_steps);
@@ -1400,15 +1421,17 @@ hotrg_status hotrg_diagnostics(hotrg_plan p, double* trunc, double* gap, int* is
   return HOTRG_OK;
 }
 
-hotrg_status hotrg_eigh_diagnostics(hotrg_plan p, double* residual, int* exact_step,
-                                    long long* fallbacks) {
+hotrg_status hotrg_eigh_diagnostics(hotrg_plan p, double* residual, int* extra_iters,
+                                    int* exact_step, long long* guard_steps) {
   if (!p) return HOTRG_EINVAL;
   const int n = p->cfg.n_steps;
   if (residual) CK(cudaMemcpy(residual, p->dres, sizeof(double) * n, cudaMemcpyDeviceToHost));
-  if (exact_step)
-    for (int k = 0; k < n; ++k)
-      exact_step[k] = (int)p->exact_step.size() == n ? p->exact_step[k] : 0;
-  if (fallbacks) *fallbacks = p->fallbacks;
+  const bool have = (int)p->exact_step.size() == n;
+  for (int k = 0; k < n; ++k) {
+    if (extra_iters) extra_iters[k] = have ? p->guard_iters[k] : 0;
+    if (exact_step) exact_step[k] = have ? p->exact_step[k] : 0;
+  }
+  if (guard_steps) *guard_steps = p->fallbacks;
   return HOTRG_OK;
 }
 
@@ -1513,8 +1536,8 @@ hotrg_status hotrg_device_supports_split(void) {
   return (prop.major == 10 && prop.minor == 3) ? HOTRG_OK : HOTRG_EUNSUPPORTED;
 }
 
-hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, const double* A,
-                                    const double* B, double* C) {
+hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk, int cta_pair,
+                                    const double* A, const double* B, double* C) {
   if (M < 1 || N < 1 || K < 8 || K % 8 != 0 || planes < 2 || planes > 4 || !A || !B || !C)
     return HOTRG_EINVAL;
   hotrg_status status = HOTRG_OK;
@@ -1550,6 +1573,7 @@ hotrg_status hotrg_gemm_split_check(int M, int N, int K, int planes, int kchunk,
   g.cm = map_lin(N); g.cn = map_lin(1);
   g.out_mode = kOutF64; g.out_planes = 1; g.C = dC; g.alpha = 1.f; g.err = err;
   g.c_lim = (long long)M * N;
+  g.cta_pair = cta_pair ? 1 : 0;
   if (tc_gemm(opnd(pa, M, K, planes, sa), opnd(pb, N, K, planes, sb), g, 0, sms) != cudaSuccess) {
     status = HOTRG_ECUDA;
     goto done;
