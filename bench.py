@@ -262,6 +262,25 @@ def c1_latency(hot, reps=30):
     return out
 
 
+def run_gemm_case(args):
+    """One split-BF16 GEMM C = A B^T (three planes, accumulation chunks of
+    128, the stage-2 kernel of the HOTRG step) of the given M, N, K on seeded
+    N(0, 1) operands, through hotrg_gemm_split_check; checks a sample of C
+    against FP64 and prints the kernel configuration.  Used as the small case
+    of ncu captures of the stage-2 kernel."""
+    import paper_1912_02780_gb300 as hot
+    M, N, K = (int(x) for x in args.gemm_case.split(","))
+    rng = np.random.default_rng(0)
+    A = rng.standard_normal((M, K))
+    B = rng.standard_normal((N, K))
+    C = hot.gemm_split_check(A, B, planes=3, kchunk=2, cta_pair=args.stage2_pair > 0)
+    rows = rng.integers(0, M, size=64)
+    ref = A[rows] @ B.T
+    err = float(np.max(np.abs(C[rows] - ref) / (np.abs(A[rows]) @ np.abs(B).T)))
+    print(json.dumps({"gemm_case": [M, N, K], "planes": 3, "cta_pair": args.stage2_pair > 0,
+                      "sampled_rel_err": err}), flush=True)
+
+
 def run_reference(args):
     """Reference arm: the FP64 CPU oracle as it stands, bounded samples."""
     rank = int(os.environ.get("RANK", "0"))
@@ -426,11 +445,11 @@ def main():
     ap.add_argument("--power-iters", type=int, default=2)
     ap.add_argument("--eigh-block", type=int, default=0,
                     help="vectors in the subspace eigensolver's block (0: 4 D_cut)")
-    ap.add_argument("--concurrent", type=int, default=2,
+    ap.add_argument("--concurrent", type=int, default=3,
                     help="independent solves (seeds) per GPU per step, each on its own "
                          "stream, so that one solve's latency-bound FP64 eigensolve overlaps "
-                         "the other's tensor-core stages (D_cut = 64: 1 / 2 / 3 / 4 gave "
-                         "0.431 / 0.485 / 0.500 / 0.504 solves/s)")
+                         "the other's tensor-core stages (D_cut = 64, warm start, 16 SMs "
+                         "reserved: 2 / 3 / 4 gave 0.619 / 0.629 / 0.603 solves/s)")
     ap.add_argument("--grad", type=int, default=0, help="1: each step is forward + backward")
     ap.add_argument("--n-steps", type=int, default=0,
                     help="override the workload's coarse-graining steps (profiling runs)")
@@ -441,6 +460,12 @@ def main():
                     help="N-tiles per L2 raster group of the stage-2 GEMM (0: library default)")
     ap.add_argument("--stage2-pair", type=int, default=0,
                     help="stage-2 GEMM on CTA pairs (0: library default, 1: on, -1: off)")
+    ap.add_argument("--sm-reserve", type=int, default=16,
+                    help="SMs the contraction GEMMs of each plan leave to the other "
+                         "concurrent solves' eigensolver kernels")
+    ap.add_argument("--warm-start", type=int, default=1,
+                    help="> 0: subspace eigensolver warm-started from step k-2 with this many "
+                         "power iterations")
     ap.add_argument("--no-c1", action="store_true", help="skip the C1 latency measurement")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -450,11 +475,16 @@ def main():
                     help="the Ising beta grid (64 betas, D_cut = 32): f, u, c and solves/s")
     ap.add_argument("--dtrg", action="store_true",
                     help="time differentiable-TRG MERA updates at the workload's size")
+    ap.add_argument("--gemm-case", default="",
+                    help="M,N,K: one three-plane split GEMM of the stage-2 kind through the "
+                         "kernel-check entry point (a small case for ncu captures)")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     args = ap.parse_args()
+    if args.gemm_case:
+        return run_gemm_case(args)
     if args.serve:
         return run_serve(args)
     if args.grid:
@@ -496,7 +526,8 @@ def main():
                       hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
                       eigh_power_iters=args.power_iters, eigh_block=args.eigh_block,
                       split_chunk_elems=args.split_chunk, stage2_n_group=args.stage2_group,
-                      stage2_pair=args.stage2_pair)
+                      stage2_pair=args.stage2_pair, gemm_sm_reserve=args.sm_reserve,
+                      eigh_warm_start=args.warm_start)
              for st in streams]
     T0_devs = [torch.tensor(t, dtype=torch.float64, device=dev) for t in T0s]
     out_devs = [torch.zeros(n + 2, dtype=torch.float64, device=dev) for _ in range(C)]

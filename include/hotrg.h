@@ -130,6 +130,16 @@ typedef struct {
                                its 128 rows of U and half of the 128-row tile of the other
                                operand); 0 = the default (one CTA per tile, measured
                                faster), > 0 = on.  Results are bit-identical either way.   */
+  int gemm_sm_reserve;      /* SMs the persistent tensor-core contraction GEMMs leave free
+                               (0..64, default 0): with several plans running concurrently on
+                               their own streams, the latency-bound eigensolver kernels of one
+                               solve then run beside the other's contractions instead of
+                               waiting for whole GEMMs.  Results do not depend on it.      */
+  int eigh_warm_start;      /* eigh_mode 1: > 0 = start the subspace block of step k from the
+                               kept eigenvectors of step k - 2 (the same leg bases near the
+                               fixed point of the flow) and run this many power iterations
+                               there instead of eigh_power_iters; the accuracy guard still
+                               checks every step.  0 = off (default), at most 16.          */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -138,7 +148,7 @@ typedef struct hotrg_plan_s* hotrg_plan;
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
  * epilogue_split = 1, split_chunk_elems = 0, w_given = 0, eigh_residual_tol = 0,
- * stage2_n_group = 0, stage2_pair = 0.
+ * stage2_n_group = 0, stage2_pair = 0, gemm_sm_reserve = 0, eigh_warm_start = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 

@@ -54,7 +54,8 @@ class hotrg_config(ctypes.Structure):
                 ("eigh_power_iters", ctypes.c_int), ("eigh_block", ctypes.c_int),
                 ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong),
                 ("w_given", ctypes.c_int), ("eigh_residual_tol", ctypes.c_double),
-                ("stage2_n_group", ctypes.c_int), ("stage2_pair", ctypes.c_int)]
+                ("stage2_n_group", ctypes.c_int), ("stage2_pair", ctypes.c_int),
+                ("gemm_sm_reserve", ctypes.c_int), ("eigh_warm_start", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -165,7 +166,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 eigh_power_iters: int = 4, eigh_block: int = 0,
                 epilogue_split: bool = True, split_chunk_elems: int = 0,
                 w_given: bool = False, eigh_residual_tol: float = 0.0,
-                stage2_n_group: int = 0, stage2_pair: int = 0) -> hotrg_config:
+                stage2_n_group: int = 0, stage2_pair: int = 0,
+                gemm_sm_reserve: int = 0, eigh_warm_start: int = 0) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -184,6 +186,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_residual_tol = float(eigh_residual_tol)
     c.stage2_n_group = int(stage2_n_group)
     c.stage2_pair = int(stage2_pair)
+    c.gemm_sm_reserve = int(gemm_sm_reserve)
+    c.eigh_warm_start = int(eigh_warm_start)
     return c
 
 
@@ -211,12 +215,13 @@ class Plan:
                  eigh_mode: int = 0, eigh_power_iters: int = 4, eigh_block: int = 0,
                  epilogue_split: bool = True, split_chunk_elems: int = 0,
                  w_given: bool = False, eigh_residual_tol: float = 0.0,
-                 stage2_n_group: int = 0, stage2_pair: int = 0):
+                 stage2_n_group: int = 0, stage2_pair: int = 0, gemm_sm_reserve: int = 0,
+                 eigh_warm_start: int = 0):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
                                epilogue_split, split_chunk_elems, w_given, eigh_residual_tol,
-                               stage2_n_group, stage2_pair)
+                               stage2_n_group, stage2_pair, gemm_sm_reserve, eigh_warm_start)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))

@@ -139,6 +139,7 @@ struct hotrg_plan_s {
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
   int sms = 152;
+  int tc_sms = 152;   // CTAs of the persistent tensor-core GEMMs (sms - gemm_sm_reserve)
   std::vector<void*> allocs;
   std::vector<size_t> alloc_bytes;
   std::vector<double*> T, E, lam;
@@ -160,6 +161,10 @@ struct hotrg_plan_s {
   std::vector<char> exact_step;
   long long fallbacks = 0;
   int* guard_host = nullptr;       // pinned host word the guard is read into
+  // warm start of the subspace eigensolver: kept eigenvectors of the last two
+  // steps (by step parity) and their shapes
+  double* wkeep[2] = {nullptr, nullptr};
+  int wkeep_n[2] = {0, 0}, wkeep_xp[2] = {0, 0};
   __nv_bfloat16 *pTA = nullptr, *pTB = nullptr, *pA = nullptr, *pB = nullptr, *pW1 = nullptr,
                 *pT1 = nullptr, *pP = nullptr, *pW3 = nullptr, *pU = nullptr, *pV = nullptr;
   float* F32 = nullptr;   // FP32 GEMM output awaiting its grid-aligned split
@@ -272,6 +277,8 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->w_given && (!c->want_grad || !c->fixed_w_grad)) return HOTRG_EINVAL;
   if (!std::isfinite(c->eigh_residual_tol) || c->eigh_residual_tol < 0) return HOTRG_EINVAL;
   if (c->stage2_n_group < 0) return HOTRG_EINVAL;
+  if (c->gemm_sm_reserve < 0 || c->gemm_sm_reserve > 64) return HOTRG_EINVAL;
+  if (c->eigh_warm_start < 0 || c->eigh_warm_start > 16) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -384,16 +391,16 @@ hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double
   TcOperand ta = opnd(p->pTA, X * Y, X * Y, np, sT), tb = opnd(p->pTB, X * Y, X * Y, np, sT);
   CK(tc_gemm(ta, ta, tcg(p, np, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2),
                          stage_mode(np), stage_buf(p, np), 0),
-             st, p->sms));
+             st, p->tc_sms));
   CK(fsplit(p, np, X * X, Y * Y, sG, p->pA));
   CK(tc_gemm(tb, tb, tcg(p, np, X * Y, X * Y, X * Y, map2(Y, Y, XY2), map2(Y, 1, Y2),
                          stage_mode(np), stage_buf(p, np), 0),
-             st, p->sms));
+             st, p->tc_sms));
   CK(fsplit(p, np, X * X, Y * Y, sG, p->pB));
   TcOperand a = opnd(p->pA, X * X, Y * Y, np, sG), b = opnd(p->pB, X * X, Y * Y, np, sG);
   CK(tc_gemm(a, b, tcg(p, np, X * X, X * X, Y * Y, map2(X, X, (long long)X * X * X),
                        map2(X, 1, (long long)X * X), kOutF64, G, 0),
-             st, p->sms));
+             st, p->tc_sms));
   return HOTRG_OK;
 }
 
@@ -491,7 +498,7 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     g1.m_fast = 1;   // the W1 tiles stay in L2; each T1 tile is read from HBM once
     g1.seg_prow = p1r;
     g1.seg_phalf = p1h;
-    CK(tc_gemm(w1, t1, g1, st, p->sms));
+    CK(tc_gemm(w1, t1, g1, st, p->tc_sms));
     if (!fuse1) CK(fsplit(p, np, yc * X * Xp, X * Y, sC, p->pU));
     }
     const TcOperand u = opnd(p->pU, yc * X * Xp, X * Y, np, sC);
@@ -504,7 +511,7 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     g2.seg_phalf = p2h;
     g2.n_group = stage2_group(p->cfg);
     g2.cta_pair = stage2_pair(p->cfg);
-    CK(tc_gemm(u, pp, g2, st, p->sms));
+    CK(tc_gemm(u, pp, g2, st, p->tc_sms));
     }
     if (!fuse2) {
     Stage sc(p, kStPrep);
@@ -515,7 +522,7 @@ hotrg_status contract_split(hotrg_plan p, const StepGeom& s, const double* T, co
     CK(tc_gemm(v, w3,
                tcg(p, np, yc * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1), kOutF64,
                    Tout + (long long)y0 * Y * Xp2, 0),
-               st, p->sms));
+               st, p->tc_sms));
   }
   return HOTRG_OK;
 }
@@ -579,7 +586,8 @@ bool subspace_on_tc(const hotrg_plan p, const StepGeom& s) {
 // resume = true continues from the orthonormal block the previous call left
 // in p->Qs with `iters` more power iterations (the accuracy guard's
 // refinement) instead of starting from the random block.
-hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step, int iters, bool resume) {
+hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step, int iters, bool resume,
+                           const double* warm = nullptr) {
   cudaStream_t st = p->stream;
   const int N = (int)s.N, K = subspace_k(p->cfg, s);
   const bool tc = subspace_on_tc(p, s);
@@ -621,8 +629,14 @@ hotrg_status eigh_subspace(hotrg_plan p, const StepGeom& s, int k_step, int iter
     Stage sc(p, kStEighQR);
     return householder();
   };
-  if (!resume)
+  if (!resume) {
     CK(fill_random(p->Qs, (long long)K * N, 0x5EEDull + (unsigned long long)k_step, st, p->sms));
+    // warm start: the first D' vectors of the block are the kept eigenvectors
+    // of step k - 2 (same leg bases near the fixed point of the flow)
+    if (warm)
+      CK(cudaMemcpyAsync(p->Qs, warm, sizeof(double) * (size_t)s.Xp * N, cudaMemcpyDeviceToDevice,
+                         st));
+  }
   hotrg_status r;
   for (int it = 0; it < iters; ++it) {
     if ((r = product()) != HOTRG_OK) return r;
@@ -733,8 +747,14 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   if (use_subspace(p, s)) {
     // randomized subspace eigensolver, checked on the device; where the check
     // fails, up to kGuardMaxIters more power iterations, then the exact solver
-    const int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
-    if ((r = eigh_subspace(p, s, k, iters, false)) != HOTRG_OK) return r;
+    int iters = p->cfg.eigh_power_iters > 0 ? p->cfg.eigh_power_iters : 4;
+    const double* warm = nullptr;
+    if (p->cfg.eigh_warm_start > 0 && k >= 3 && p->wkeep[k & 1] &&
+        p->wkeep_n[k & 1] == N && p->wkeep_xp[k & 1] == s.Xp) {
+      warm = p->wkeep[k & 1];
+      iters = p->cfg.eigh_warm_start;
+    }
+    if ((r = eigh_subspace(p, s, k, iters, false, warm)) != HOTRG_OK) return r;
     if ((r = finish(p->Zs, subspace_ritz(s))) != HOTRG_OK) return r;
     if ((r = eigh_residual(p, s, k)) != HOTRG_OK) return r;
     bool fired = false;
@@ -770,6 +790,13 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     if ((r = finish(p->Escr, ncols)) != HOTRG_OK) return r;
     CK(set_value(p->dres + (k - 1), std::nan(""), nullptr, 0, st));
   }
+  if (p->wkeep[k & 1]) {
+    // this step's kept eigenvectors: the warm start of step k + 2
+    CK(cudaMemcpyAsync(p->wkeep[k & 1], Ek, sizeof(double) * (size_t)s.Xp * N,
+                       cudaMemcpyDeviceToDevice, st));
+    p->wkeep_n[k & 1] = N;
+    p->wkeep_xp[k & 1] = s.Xp;
+  }
   }
   }
   if (s.split) r = contract_split(p, s, T, Ek, Tout);
@@ -790,6 +817,7 @@ hotrg_status run_forward(hotrg_plan p) {
     return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
   p->have_bwd = false;
   p->guard_iters.assign(p->cfg.n_steps, 0);
+  p->wkeep_n[0] = p->wkeep_n[1] = 0;   // no warm start across forwards
   p->exact_step.assign(p->cfg.n_steps, 0);
   for (int k = 1; k <= p->cfg.n_steps; ++k) {
     hotrg_status r = step_forward(p, k);
@@ -841,7 +869,7 @@ cudaError_t run_gemm(hotrg_plan p, int np, const GemmF64& g, unsigned f32 = 0) {
   t.alpha = (float)g.alpha;
   t.accumulate = g.beta != 0.0 ? 1 : 0;
   return tc_gemm(opnd(p->pU, g.M, g.K, np, cap), opnd(p->pV, g.N, g.K, np, cap), t, p->stream,
-                 p->sms);
+                 p->tc_sms);
 }
 
 hotrg_status step_backward(hotrg_plan p, int k) {
@@ -1083,6 +1111,8 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_residual_tol = 0.0;
   c->stage2_n_group = 0;
   c->stage2_pair = 0;
+  c->gemm_sm_reserve = 0;
+  c->eigh_warm_start = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -1149,6 +1179,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   cudaDeviceProp prop;
   if (cudaGetDeviceProperties(&prop, dev) != cudaSuccess) return cleanup(HOTRG_ECUDA);
   p->sms = prop.multiProcessorCount;
+  p->tc_sms = std::max(1, p->sms - cfg->gemm_sm_reserve);
   if (p->L.any_split && !(prop.major == 10 && prop.minor == 3)) return cleanup(HOTRG_EUNSUPPORTED);
   const Layout& L = p->L;
   const int n = cfg->n_steps;
@@ -1261,6 +1292,10 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     p->svd_lwork = ls;
     ALC(p->svd_work, (long long)ls);
     ALC(p->svd_rwork, L.maxXp);
+  }
+  if (cfg->eigh_mode == 1 && !cfg->want_grad && cfg->eigh_warm_start > 0) {
+    ALC(p->wkeep[0], L.maxN * L.maxXp);
+    ALC(p->wkeep[1], L.maxN * L.maxXp);
   }
   if (cfg->eigh_mode == 1 && !cfg->want_grad) {
     int kmax = 0;

@@ -48,5 +48,9 @@ def test_autograd_split_gradient_close_to_oracle():
     T0 = torch.tensor(T0n, dtype=torch.float64, device="cuda", requires_grad=True)
     ag.lnz(T0, plan).backward()
     g = T0.grad.cpu().numpy()
-    assert np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref)) < 5e-6
+    # seed 1 at D_cut = 16 has no near-degenerate cut (smallest relative gap
+    # 1.5e-5), so the split backward's 1e-6 gradient target applies
+    err = np.max(np.abs(g - g_ref)) / np.max(np.abs(g_ref))
+    print(f"autograd split gradient: rel err {err:.2e}")
+    assert err < 1e-6
     plan.close()

@@ -229,22 +229,26 @@ def test_fp64_gradient_against_finite_differences_c3_reduced():
     assert err < 1e-6
 
 
-@pytest.mark.parametrize("seed,iters,split_from,hi", [(0, 2, 4, 3), (1, 2, 4, 3), (2, 2, 4, 3),
-                                                      (0, 3, 4, 3), (0, 2, 5, 2), (1, 2, 5, 2)])
-def test_subspace_eigensolver_c4_d64_against_stored_oracle(seed, iters, split_from, hi):
+@pytest.mark.parametrize("seed,iters,split_from,hi,warm", [
+    (0, 2, 4, 3, 0), (1, 2, 4, 3, 0), (2, 2, 4, 3, 0), (0, 3, 4, 3, 0), (0, 2, 5, 2, 0),
+    (1, 2, 5, 2, 0), (0, 2, 4, 3, 1), (1, 2, 4, 3, 1), (2, 2, 4, 3, 1), (3, 2, 4, 3, 1),
+    (4, 2, 4, 3, 1)])
+def test_subspace_eigensolver_c4_d64_against_stored_oracle(seed, iters, split_from, hi, warm):
     """Forward with the randomized subspace eigensolver (eigh_mode 1: block
-    power iteration on 4 D' vectors + Rayleigh-Ritz) in the benchmark's
-    configuration (FP64 steps 1-3, four bf16 planes on steps 4-6, three after)
-    and with FP64 steps 1-4, four planes on 5-6: within 1e-9 of the oracle's
-    ln Z / N."""
+    power iteration on 4 D' vectors + Rayleigh-Ritz, with its accuracy guard)
+    in the benchmark's configuration (FP64 steps 1-3, four bf16 planes on
+    steps 4-6, three after; warm start from step k - 2 with one power
+    iteration, seeds 0-4) and with cold starts, FP64 steps 1-4, four planes on
+    5-6: within 1e-9 of the oracle's ln Z / N."""
     g = _golden(f"c4_d64_s{seed}")
     T0 = synth.random_symmetric_T0(seed, 4)
     with hot.Plan(4, 64, 30, "bf16x6", split_from_step=split_from, want_grad=False,
-                  hi_precision_steps=hi, eigh_mode=1, eigh_power_iters=iters) as p:
+                  hi_precision_steps=hi, eigh_mode=1, eigh_power_iters=iters,
+                  eigh_warm_start=warm, gemm_sm_reserve=16 if warm else 0) as p:
         lnz, _, sign = p.forward_tensor(T0)
         tr, _, _ = p.diagnostics()
     err = abs(lnz - g["lnz"])
-    print(f"subspace eigh iters={iters} split {split_from}/{hi}: |dlnz| = {err:.3e}")
+    print(f"subspace eigh iters={iters} warm={warm} split {split_from}/{hi}: |dlnz| = {err:.3e}")
     assert sign == g["trace_sign"]
     assert err < 1e-9
     assert np.max(np.abs(tr - np.array(g["trunc_err"]))) < 1e-7
@@ -351,3 +355,19 @@ def test_gemm_split_cta_pair_equals_single_cta(M, N, K, kchunk):
     assert np.array_equal(C1, C2)
     scale = np.abs(A) @ np.abs(B).T
     assert np.max(np.abs(C2 - A @ B.T) / scale) < (5e-8 if kchunk == 2 and K >= 512 else 4e-6)
+
+
+def test_sm_reserve_does_not_change_results():
+    """Leaving SMs free in the contraction GEMMs changes only how many
+    persistent CTAs walk the tiles, not any sum: bit-identical results."""
+    T0 = synth.random_symmetric_T0(1, 4)
+    out = []
+    for reserve in (0, 16, 37):
+        with hot.Plan(4, 32, 10, "bf16x6", split_from_step=3, want_grad=True,
+                      gemm_sm_reserve=reserve) as p:
+            lnz, ln, _ = p.forward_tensor(T0)
+            g = p.backward()
+        out.append((lnz, np.array(ln), g))
+    for o in out[1:]:
+        assert o[0] == out[0][0]
+        assert np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])

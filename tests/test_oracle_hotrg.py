@@ -167,6 +167,45 @@ def test_tensor_gradient_matches_finite_differences(seed, d_cut, n):
     assert np.max(np.abs(g[sel] - fd[sel])) / np.max(np.abs(g)) < 1e-6
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("seed,d_cut,n", [(0, 6, 6), (1, 9, 7)])
+def test_tensor_gradient_matches_finite_differences_all_entries(seed, d_cut, n):
+    """The same pin on every one of the 81 entries of T0 (central differences,
+    eps = 1e-6, FD error ~1e-10 relative)."""
+    T0 = synth.random_symmetric_T0(seed, 3)
+    f, g = grad_full(T0, d_cut, n)
+    e = 1e-6
+    fd = np.zeros_like(T0)
+    for idx in np.ndindex(T0.shape):
+        tp, tm = T0.copy(), T0.copy()
+        tp[idx] += e
+        tm[idx] -= e
+        fd[idx] = (hotrg.hotrg_forward(tp, d_cut, n, keep=False)["lnz"]
+                   - hotrg.hotrg_forward(tm, d_cut, n, keep=False)["lnz"]) / (2 * e)
+    assert np.max(np.abs(g - fd)) / np.max(np.abs(fd)) < 1e-6
+
+
+@pytest.mark.slow
+def test_near_critical_error_at_truncation_level_d16_n30():
+    """Onsager at beta_c on the 2^15 x 2^15 torus (n = 30, finite-size terms
+    ~1/L^2 far below the truncation error) with D_cut = 16: within 1e-4."""
+    ons = exact.onsager_lnz_1d(synth.BETA_C)
+    f = hotrg.hotrg_forward(ising.ising_T0(synth.BETA_C), 16, 30, keep=False)
+    assert abs(f["lnz"] - ons) < 1e-4
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("beta", [0.30, 0.60])
+def test_converges_to_onsager_off_critical_d16_n30(beta):
+    """Off criticality the error falls with D_cut (4, 8, 16) on the 2^15 x
+    2^15 torus and is below 1e-7 at D_cut = 16."""
+    ons = exact.onsager_lnz_1d(beta)
+    errs = [abs(hotrg.hotrg_forward(ising.ising_T0(beta), d, 30, keep=False)["lnz"] - ons)
+            for d in (4, 8, 16)]
+    assert errs[2] < errs[0]
+    assert errs[2] < 1e-7
+
+
 def test_fixed_w_gradient_matches_frozen_isometry_differences():
     T0 = synth.random_symmetric_T0(4, 3)
     d_cut, n = 6, 6
