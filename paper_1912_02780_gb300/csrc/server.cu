@@ -135,6 +135,10 @@ void worker(hotrg_server_s* s, int slot) {
     // backward's eigensolve adjoint needs all eigenpairs)
     cfg.eigh_mode = r.want_grad ? 0 : 1;
     cfg.eigh_power_iters = 2;
+    cfg.eigh_warm_start = r.want_grad ? 0 : 1;
+    // with several slots, the contraction GEMMs leave SMs to the other
+    // requests' latency-bound eigensolver kernels
+    cfg.gemm_sm_reserve = s->caches.size() > 1 ? 16 : 0;
     size_t bytes = 0;
     hotrg_status st = hotrg_plan_workspace_bytes(&cfg, &bytes);
     hotrg_plan plan = nullptr;
