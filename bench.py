@@ -87,11 +87,11 @@ def products_of_step(k, split_from, hi_steps, precision):
 # dram__bytes_write.sum) of the tensor-core GEMM source with this SHA-256; the
 # value is reported only while csrc/gemm_tc.cu is unchanged since the capture.
 STAGE2_TRAFFIC = {
-    "gemm_tc_sha256": "0119a895d4c7e7486ad82abc3546161c0285544344c43229b1b8f3f617ea9ced",
+    "gemm_tc_sha256": "2560578679a3c54ebac416b14361e556950e92d342b88e2d0a1c9b8ede2ae711",
     # full-size D = 64 three-plane stage-2 launch (step 7 of the benchmark's
-    # solve), one-pass ncu capture: 128.11 GB read + 8.26 GB written (the
-    # source has changed since only in its header comment)
-    "bytes_per_launch_d64": 128.11e9 + 8.26e9,
+    # solve: N-tile groups of 16, 136 CTAs with 16 SMs reserved), one-pass ncu
+    # capture: 59.58 GB read + 8.76 GB written
+    "bytes_per_launch_d64": 59.58e9 + 8.76e9,
     "captured": "profiles/tc_gemm_stage2_c4_d64.md"}
 
 
@@ -579,19 +579,41 @@ def main():
     value = solves / (ms_total / 1e3)
     lnzs = [float(o[0].item()) for o in out_devs]
 
-    # one solve alone with per-stage CUDA events on its stream: stage breakdown
-    # and the roofline of the stage-2 kernel (not overlapped with other solves)
-    plans[0].profile(True)
-    t_a = torch.cuda.Event(enable_timing=True)
-    t_b = torch.cuda.Event(enable_timing=True)
-    t_a.record(streams[0])
-    solve_dev(0)
-    t_b.record(streams[0])
-    torch.cuda.synchronize(dev)
-    prof = plans[0].profile_read()
-    plans[0].profile(False)
-    single_ms = t_a.elapsed_time(t_b)
     guard = [pl.eigh_diagnostics() for pl in plans]
+
+    # one solve alone with per-stage CUDA events on its stream: stage breakdown
+    # and the roofline of the stage-2 kernel (not overlapped with other solves).
+    # Timed twice: with the timed region's plan (its contraction GEMMs leave
+    # --sm-reserve SMs to the other solves) and with a plan whose GEMMs use
+    # every SM, which is the kernel's own roofline.
+    def profiled_solve(plan, i):
+        plan.profile(True)
+        t_a = torch.cuda.Event(enable_timing=True)
+        t_b = torch.cuda.Event(enable_timing=True)
+        t_a.record(streams[i])
+        plan.forward_device(T0_devs[i].data_ptr(), out_devs[i].data_ptr())
+        if args.grad:
+            plan.backward_device(grad_devs[i].data_ptr())
+        plan.sync()
+        t_b.record(streams[i])
+        torch.cuda.synchronize(dev)
+        pr = plan.profile_read()
+        plan.profile(False)
+        return pr, t_a.elapsed_time(t_b)
+
+    prof_bench, single_ms_bench = profiled_solve(plans[0], 0)
+    prof, single_ms = prof_bench, single_ms_bench
+    if args.sm_reserve > 0:
+        with hot.Plan(d0, d_cut, n, args.precision, split_from_step=args.split_from,
+                      want_grad=bool(args.grad), stream=streams[0].cuda_stream,
+                      hi_precision_steps=args.hi_steps, eigh_mode=args.eigh_mode,
+                      eigh_power_iters=args.power_iters, eigh_block=args.eigh_block,
+                      split_chunk_elems=args.split_chunk, stage2_n_group=args.stage2_group,
+                      stage2_pair=args.stage2_pair, gemm_sm_reserve=0,
+                      eigh_warm_start=args.warm_start) as pfull:
+            pfull.forward_device(T0_devs[0].data_ptr(), out_devs[0].data_ptr())
+            pfull.sync()
+            prof, single_ms = profiled_solve(pfull, 0)
 
     # useful / executed flops of one solve and of the stage-2 launches
     sched = schedule(d0, d_cut, n)
@@ -625,6 +647,13 @@ def main():
         if (STAGE2_TRAFFIC["gemm_tc_sha256"] == gemm_source_sha() and d_cut == 64
                 and STAGE2_TRAFFIC["bytes_per_launch_d64"]):
             traffic = STAGE2_TRAFFIC["bytes_per_launch_d64"]
+        in_bench = None
+        if "s2" in prof_bench and args.sm_reserve > 0:
+            b_ms = prof_bench["s2"][0] / prof_bench["s2"][1]
+            b_ach = exec_per_launch / (b_ms / 1e3) / 1e12
+            ctas = 152 - args.sm_reserve
+            in_bench = {"ctas": ctas, "ms_per_launch": b_ms, "achieved": b_ach,
+                        "frac_of_peak_scaled_to_ctas": b_ach / (peak * ctas / 152) if peak else None}
         roof = {"kernel": "tc_gemm_kernel<128,3> (stage 2, O(D^7), three-plane steps)",
                 "bound": "tensor",
                 "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
@@ -633,7 +662,9 @@ def main():
                 "useful_per_launch_tflop": s2_tc_useful / s2_launches / 1e12,
                 "executed_per_launch_tflop": exec_per_launch / 1e12,
                 "ms_per_launch": s2_ms_per_launch,
-                "timed": "CUDA events around every stage-2 launch of one solve run alone"}
+                "timed": "CUDA events around every stage-2 launch of one solve run alone, "
+                         "its GEMMs on every SM",
+                "in_timed_region_config": in_bench}
 
     line = {"metric": "solves/s", "value": value, "unit": "solves/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_per_step,
@@ -653,11 +684,12 @@ def main():
             "useful_tflops": useful_tflops,
             "executed_tc_tflop_per_solve": executed_tc / 1e12,
             "single_solve_ms": single_ms,
+            "single_solve_ms_timed_config": single_ms_bench,
             "lnz_per_site": lnzs,
             "stage_ms_per_solve": {k: v[0] for k, v in prof.items()},
             "gpu_launches": int(launches),
-            "eigh_guard": {"bound": "2^-k r_k <= 5e-9 (r_k: relative residual of the kept "
-                                    "Ritz pairs at step k), else up to two more power "
+            "eigh_guard": {"bound": "2^-k r_k <= 1e-9 (r_k: relative residual of the kept "
+                                    "Ritz pairs at step k), else up to four more power "
                                     "iterations, then the exact eigensolver",
                            "max_residual": [float(np.nanmax(g_[0])) if np.any(np.isfinite(g_[0]))
                                             else None for g_ in guard],

@@ -113,8 +113,8 @@ typedef struct {
   double eigh_residual_tol; /* eigh_mode 1: accuracy guard of the subspace eigensolver.  After
                                the subspace solve of step k the kept Ritz pairs are checked on
                                the device, r_k = max_a ||G v_a - theta_a v_a||_2 / theta_1.
-                               Where 2^-k r_k exceeds this bound (<= 0: 5e-9; an error at step
-                               k enters ln Z / N with weight 2^-k) the step gets up to two more
+                               Where 2^-k r_k exceeds this bound (<= 0: 1e-9; an error at step
+                               k enters ln Z / N with weight 2^-k) the step gets up to four more
                                power iterations, each checked again, and if it still fails the
                                exact partial eigensolver (cuSOLVER syevdx).  Reading the check
                                costs one host synchronisation per subspace step.  Must be

@@ -23,9 +23,12 @@ MIX = [  # (beta, h, d_cut, n_steps, want_grad, precision, split_from)
 
 def alone(beta, h, d_cut, n, grad, prec, sf):
     # the server's configuration of a request: forward-only requests use the
-    # randomized subspace eigensolver with two power iterations
+    # randomized subspace eigensolver with two power iterations, warm-started
+    # from step k - 2 (the SMs the server's plans leave free do not change
+    # any result)
     with hot.Plan(2, d_cut, n, prec, split_from_step=sf, want_grad=grad,
-                  eigh_mode=0 if grad else 1, eigh_power_iters=2) as p:
+                  eigh_mode=0 if grad else 1, eigh_power_iters=2,
+                  eigh_warm_start=0 if grad else 1) as p:
         lnz, _, _ = p.forward_ising(beta, 1.0, h)
         db = p.backward(want_dbeta=True)[1] if grad else 0.0
     return lnz, db
