@@ -313,38 +313,99 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def run_serve(args):
-    """Continuous-batching serving run: seeded Poisson arrivals of Ising solves
-    (beta ~ U[0.30, 0.60], h ~ U[0, 0.05], D_cut in {16, 24, 32, 48, 64},
-    n_steps in [20, 40], half of them with gradients), replayed in real time
-    into the solve server; latency = finish - submit on the server's clock."""
-    import paper_1912_02780_gb300 as hot
-    stream = synth.serving_stream(seed=2024, n=args.requests, rate=args.rate)
-    srv = hot.Server(int(args.budget_gb * 2 ** 30), args.slots)
+def serve_replay(hot, reqs, rate, slots, budget_gb, precision, split_from, srv=None):
+    """Replay requests into the solve server in real time: request i arrives at
+    its seeded Poisson time (synth.serving_stream, mean gap 1 / rate; rate =
+    inf submits them all at once).  Latency = finish - submit on the server's
+    clock.  Returns a dict of throughput and latency statistics."""
+    own = srv is None
+    if own:
+        srv = hot.Server(int(budget_gb * 2 ** 30), slots)
+    st0 = srv.stats()
     t0 = time.perf_counter()
     tickets = []
-    for r in stream:
-        dt = r["t_arrival"] - (time.perf_counter() - t0)
-        if dt > 0:
-            time.sleep(dt)
+    base = reqs[0]["t_arrival"]
+    for r in reqs:
+        if np.isfinite(rate):
+            # the stream's arrival times were drawn at rate 1: rescale
+            dt = (r["t_arrival"] - base) / rate - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
         tickets.append(srv.submit(r["beta"], r["J"], r["h"], r["d_cut"], r["n_steps"],
-                                  r["want_grad"], args.precision, args.split_from))
+                                  r["want_grad"], precision, split_from))
     res = [srv.wait(t) for t in tickets]
     st = srv.stats()
-    srv.close()
+    if own:
+        srv.close()
     lat = np.array([x.t_finish - x.t_submit for x in res])
     svc = np.array([x.t_finish - x.t_start for x in res])
     span = max(x.t_finish for x in res) - min(x.t_submit for x in res)
     ok = sum(1 for x in res if x.status == 0)
-    line = {"metric": "serving latency p50/p99 (s)", "value": float(np.percentile(lat, 50)),
-            "p99": float(np.percentile(lat, 99)), "unit": "s", "higher_is_better": False,
-            "solves_per_s": ok / span, "offered_rate": args.rate,
-            "achieved_rate": ok / span, "requests": len(res), "ok": ok,
-            "service_time_mean_s": float(svc.mean()), "slots": args.slots,
-            "budget_gb": args.budget_gb, "peak_gb": st["peak_bytes"] / 2 ** 30,
-            "plans_created": st["plans_created"], "plans_evicted": st["plans_evicted"],
-            "precision": args.precision, "split_from_step": args.split_from,
-            "data": "synthetic", "config": {"workload": "ising serving stream", "seed": 2024}}
+    return {"requests": len(res), "ok": ok, "offered_rate": float(rate),
+            "achieved_rate": ok / span, "p50_s": float(np.percentile(lat, 50)),
+            "p99_s": float(np.percentile(lat, 99)), "max_s": float(lat.max()),
+            "service_time_mean_s": float(svc.mean()),
+            "plans_created": st["plans_created"] - st0["plans_created"],
+            "plans_evicted": st["plans_evicted"] - st0["plans_evicted"],
+            "admission_waits": st["admission_waits"] - st0["admission_waits"],
+            "peak_gb": st["peak_bytes"] / 2 ** 30}
+
+
+def serving_stream_c5(n):
+    """The C5 request mix at unit rate (beta ~ U[0.30, 0.60], h ~ U[0, 0.05],
+    D_cut in {16, 24, 32, 48, 64}, n_steps in [20, 40], half with gradients)."""
+    return synth.serving_stream(seed=2024, n=n, rate=1.0)
+
+
+def serving_sample(hot, args, n_burst=12, n_rate=32, frac=0.5):
+    """Short serving measurement for the default benchmark line: the first
+    n_burst requests of the C5 stream submitted at once give the capacity
+    (completed requests / makespan; this also builds the plans), then the next
+    n_rate arrive as a Poisson stream at frac x capacity."""
+    stream = serving_stream_c5(n_burst + n_rate)
+    srv = hot.Server(int(args.budget_gb * 2 ** 30), args.slots)
+    burst = serve_replay(hot, stream[:n_burst], float("inf"), args.slots, args.budget_gb,
+                         args.precision, args.split_from, srv)
+    cap = burst["achieved_rate"]
+    point = serve_replay(hot, stream[n_burst:], frac * cap, args.slots, args.budget_gb,
+                         args.precision, args.split_from, srv)
+    srv.close()
+    return {"mix": "C5 (seed 2024): beta U[0.30,0.60], h U[0,0.05], D_cut {16,24,32,48,64}, "
+                   "n_steps [20,40], half with gradients",
+            "slots": args.slots, "budget_gb": args.budget_gb,
+            "capacity_req_per_s": cap, "capacity_from": f"{n_burst} requests submitted at once",
+            "rate_point": point,
+            "note": f"p99 of {n_rate} requests (about their maximum); bench.py --serve runs "
+                    f"longer rate sweeps"}
+
+
+def run_serve(args):
+    """Continuous-batching serving run on the C5 mix: the capacity from a burst
+    of requests submitted at once, then Poisson streams at the given fractions
+    of that capacity (--rates), --requests each, replayed in real time into
+    the solve server; latency = finish - submit on the server's clock."""
+    import paper_1912_02780_gb300 as hot
+    fracs = [float(x) for x in args.rates.split(",")]
+    n_burst = 16
+    stream = serving_stream_c5(n_burst + args.requests * len(fracs))
+    srv = hot.Server(int(args.budget_gb * 2 ** 30), args.slots)
+    burst = serve_replay(hot, stream[:n_burst], float("inf"), args.slots, args.budget_gb,
+                         args.precision, args.split_from, srv)
+    cap = burst["achieved_rate"]
+    points = []
+    for i, fr in enumerate(fracs):
+        reqs = stream[n_burst + i * args.requests:n_burst + (i + 1) * args.requests]
+        pt = serve_replay(hot, reqs, fr * cap, args.slots, args.budget_gb, args.precision,
+                          args.split_from, srv)
+        pt["fraction_of_capacity"] = fr
+        points.append(pt)
+        print(json.dumps(pt), flush=True)
+    srv.close()
+    line = {"metric": "serving latency p50/p99 (s)", "unit": "s", "higher_is_better": False,
+            "capacity_req_per_s": cap, "burst": burst, "points": points, "slots": args.slots,
+            "budget_gb": args.budget_gb, "precision": args.precision,
+            "split_from_step": args.split_from, "data": "synthetic",
+            "config": {"workload": "ising serving stream (C5 mix)", "seed": 2024}}
     print(json.dumps(line), flush=True)
 
 
@@ -480,6 +541,10 @@ def main():
                          "kernel-check entry point (a small case for ncu captures)")
     ap.add_argument("--requests", type=int, default=64)
     ap.add_argument("--rate", type=float, default=200.0, help="offered requests per second")
+    ap.add_argument("--rates", default="0.25,0.5,0.9",
+                    help="--serve: offered load as fractions of the measured capacity")
+    ap.add_argument("--no-serving", action="store_true",
+                    help="skip the short serving measurement of the default run")
     ap.add_argument("--slots", type=int, default=4)
     ap.add_argument("--budget-gb", type=float, default=160.0)
     args = ap.parse_args()
@@ -773,6 +838,15 @@ def main():
 
     if rank == 0 and not args.no_c1:
         line["c1_latency"] = c1_latency(hot)
+
+    if rank == 0 and world == 1 and not args.no_serving:
+        # the other solves' plans are released first: the server has the device
+        pool.shutdown()
+        for p_ in plans:
+            p_.close()
+        plans = []
+        torch.cuda.synchronize(dev)
+        line["serving"] = serving_sample(hot, args)
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         dt, fl = oracle_sample(d_cut)

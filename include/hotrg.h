@@ -281,6 +281,7 @@ typedef struct {
   uint64_t submitted, completed, failed, plans_created, plans_evicted;
   size_t bytes_in_use, peak_bytes;
   int queue_depth, busy_slots;
+  uint64_t admission_waits;  /* requests that waited for device memory before their plan */
 } hotrg_server_stats;
 hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_server* out);
 hotrg_status hotrg_server_submit(hotrg_server server, const hotrg_request* req, uint64_t* ticket);

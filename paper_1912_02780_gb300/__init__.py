@@ -76,7 +76,7 @@ class hotrg_server_stats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("plans_created", ctypes.c_uint64),
                 ("plans_evicted", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("queue_depth", ctypes.c_int),
-                ("busy_slots", ctypes.c_int)]
+                ("busy_slots", ctypes.c_int), ("admission_waits", ctypes.c_uint64)]
 
 
 class HotrgError(RuntimeError):

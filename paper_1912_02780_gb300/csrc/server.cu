@@ -65,6 +65,7 @@ struct hotrg_server_s {
   std::vector<int> busy;
   size_t bytes_in_use = 0, peak_bytes = 0;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, created = 0, evicted = 0;
+  uint64_t admission_waits = 0;   // requests that had to wait for device memory
   int trim_epoch = 0;
   int running = 0;
   bool stop = false;
@@ -157,6 +158,7 @@ void worker(hotrg_server_s* s, int slot) {
         st = HOTRG_ENOMEM;
       } else {
         trim_own(s, slot, bytes, lk);
+        if (s->bytes_in_use + bytes > s->budget) s->admission_waits += 1;
         while (s->bytes_in_use + bytes > s->budget) {
           // ask idle slots to free their cached plans, then wait for memory
           s->trim_epoch += 1;
@@ -274,6 +276,7 @@ hotrg_status hotrg_server_get_stats(hotrg_server s, hotrg_server_stats* o) {
   o->peak_bytes = s->peak_bytes;
   o->plans_created = s->created;
   o->plans_evicted = s->evicted;
+  o->admission_waits = s->admission_waits;
   o->queue_depth = (int)s->queue.size();
   o->busy_slots = s->running;
   return HOTRG_OK;
