@@ -546,7 +546,7 @@ def main():
     ap.add_argument("--no-serving", action="store_true",
                     help="skip the short serving measurement of the default run")
     ap.add_argument("--slots", type=int, default=4)
-    ap.add_argument("--budget-gb", type=float, default=160.0)
+    ap.add_argument("--budget-gb", type=float, default=240.0)
     args = ap.parse_args()
     if args.gemm_case:
         return run_gemm_case(args)

@@ -220,6 +220,14 @@ hotrg_status hotrg_backward(hotrg_plan plan, double* dlnz_dT0_host, double* dlnz
 /* Device-resident backward: writes d(ln Z/N)/d T0 (d0^4 float64) to grad_dev. */
 hotrg_status hotrg_backward_device(hotrg_plan plan, double* grad_dev);
 
+/* Run only the first n_steps (1 <= n_steps <= the plan's n_steps) in the
+ * following forwards and backwards: the result is that of a plan created with
+ * n_steps (bit for bit: every step depends only on the steps before it), so one
+ * plan serves requests of any depth up to its own.  Output arrays
+ * (log_norms, out_dev) then hold n_steps + 2 / n_steps values; the per-step
+ * diagnostics keep the plan's length, with entries past n_steps stale. */
+hotrg_status hotrg_plan_set_steps(hotrg_plan plan, int n_steps);
+
 /* Wait for the plan's stream and report any device-side failure. */
 hotrg_status hotrg_sync(hotrg_plan plan);
 
@@ -257,8 +265,10 @@ hotrg_status hotrg_device_supports_split(void);
  * while others are on the GPU start as soon as a slot and device memory are
  * free and their kernels overlap on the device.  Every live plan is charged
  * its hotrg_plan_workspace_bytes against hbm_budget_bytes; slots keep built
- * plans for reuse by later requests of the same shape and free idle ones when
- * a new plan would not fit.  A request whose plan alone exceeds the budget
+ * plans for reuse by later requests of the same D_cut, precision and gradient
+ * need (plans are built for 40 steps, or the request's depth if larger or if
+ * a 40-step plan would not fit the budget, and run each request's own depth)
+ * and free idle ones when a new plan would not fit.  A request whose plan alone exceeds the budget
  * finishes with status HOTRG_ENOMEM.  Requests without gradients use the
  * randomized subspace eigensolver (eigh_mode 1, 2 power iterations).  Times are seconds since the server was
  * created.  Submit, poll, wait, drain and stats are thread-safe. */

@@ -31,6 +31,7 @@ EXPORTS = (
     "hotrg_isometries", "hotrg_set_isometries", "hotrg_isometry_adjoints", "hotrg_mera_update", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
+    "hotrg_plan_set_steps",
     "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
     L.hotrg_backward.argtypes = [vp, _dp, _dp]
     L.hotrg_backward_device.argtypes = [vp, vp]
     L.hotrg_sync.argtypes = [vp]
+    L.hotrg_plan_set_steps.argtypes = [vp, ctypes.c_int]
     L.hotrg_diagnostics.argtypes = [vp, _dp, _dp, _ip]
     L.hotrg_step_dims.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip]
     L.hotrg_eigh_diagnostics.argtypes = [vp, _dp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)]
@@ -223,6 +225,7 @@ class Plan:
                                epilogue_split, split_chunk_elems, w_given, eigh_residual_tol,
                                stage2_n_group, stage2_pair, gemm_sm_reserve, eigh_warm_start)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
+        self.n_run = n_steps
         h = ctypes.c_void_p(0)
         s = lib().hotrg_plan_create(ctypes.byref(self.cfg), ctypes.c_void_p(stream or 0), ctypes.byref(h))
         if s:
@@ -234,12 +237,18 @@ class Plan:
             msg = lib().hotrg_last_error(self._h)
             raise HotrgError(s, f"{what}: {msg.decode() if msg else ''}")
 
+    def set_steps(self, n_steps: int):
+        """Run only the first n_steps of this plan from now on (the result of
+        a plan created with n_steps)."""
+        self._check(lib().hotrg_plan_set_steps(self._h, int(n_steps)), "set_steps")
+        self.n_run = int(n_steps)
+
     def forward_tensor(self, T0: np.ndarray):
         T0 = np.ascontiguousarray(T0, dtype=np.float64)
         if T0.shape != (self.d0,) * 4:
             raise ValueError("T0 must have shape (d0, d0, d0, d0)")
         lnz = ctypes.c_double(0)
-        ln = np.zeros(self.n_steps)
+        ln = np.zeros(self.n_run)
         sign = ctypes.c_int(0)
         self._check(lib().hotrg_forward_tensor(self._h, _p(T0), ctypes.byref(lnz), _p(ln),
                                                ctypes.byref(sign)), "forward_tensor")
@@ -247,7 +256,7 @@ class Plan:
 
     def forward_ising(self, beta: float, J: float = 1.0, h: float = 0.0):
         lnz = ctypes.c_double(0)
-        ln = np.zeros(self.n_steps)
+        ln = np.zeros(self.n_run)
         sign = ctypes.c_int(0)
         self._check(lib().hotrg_forward_ising(self._h, beta, J, h, ctypes.byref(lnz), _p(ln),
                                               ctypes.byref(sign)), "forward_ising")

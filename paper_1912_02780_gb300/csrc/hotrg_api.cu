@@ -135,6 +135,7 @@ struct Bytes {
 
 struct hotrg_plan_s {
   hotrg_config cfg;
+  int n_run = 0;      // steps the forward and backward run (<= cfg.n_steps)
   Layout L;
   cudaStream_t stream = nullptr;
   cusolverDnHandle_t solver = nullptr;
@@ -821,12 +822,12 @@ hotrg_status run_forward(hotrg_plan p) {
   p->guard_iters.assign(p->cfg.n_steps, 0);
   p->wkeep_n[0] = p->wkeep_n[1] = 0;   // no warm start across forwards
   p->exact_step.assign(p->cfg.n_steps, 0);
-  for (int k = 1; k <= p->cfg.n_steps; ++k) {
+  for (int k = 1; k <= p->n_run; ++k) {
     hotrg_status r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
   }
-  const StepGeom& last = p->L.g.back();
-  CK(trace_lnz(p->T[p->cfg.n_steps], last.Y, last.Xp, p->log_norms, p->cfg.n_steps, p->out,
+  const StepGeom& last = p->L.g[p->n_run - 1];
+  CK(trace_lnz(p->T[p->n_run], last.Y, last.Xp, p->log_norms, p->n_run, p->out,
                p->scal + 1, p->err, st));
   return HOTRG_OK;
 }
@@ -986,9 +987,9 @@ hotrg_status step_backward(hotrg_plan p, int k) {
 }
 
 hotrg_status run_backward(hotrg_plan p) {
-  const StepGeom& last = p->L.g.back();
+  const StepGeom& last = p->L.g[p->n_run - 1];
   CK(seed_trace_adjoint(p->Ecur, last.Y, last.Xp, p->scal + 1, p->stream, p->sms));
-  for (int k = p->cfg.n_steps; k >= 1; --k) {
+  for (int k = p->n_run; k >= 1; --k) {
     hotrg_status r = step_backward(p, k);
     if (r != HOTRG_OK) return r;
   }
@@ -1167,6 +1168,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   if (validate(cfg) != HOTRG_OK) return HOTRG_EINVAL;
   hotrg_plan p = new hotrg_plan_s();
   p->cfg = *cfg;
+  p->n_run = cfg->n_steps;
   if (!build_layout(*cfg, p->L)) {
     delete p;
     return HOTRG_EINVAL;
@@ -1361,7 +1363,7 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
   hotrg_status r = run_forward(p);
   if (r != HOTRG_OK) return r;
   if (out_dev)
-    CK(cudaMemcpyAsync(out_dev, p->out, sizeof(double) * (p->cfg.n_steps + 2),
+    CK(cudaMemcpyAsync(out_dev, p->out, sizeof(double) * (p->n_run + 2),
                        cudaMemcpyDeviceToDevice, p->stream));
   p->have_fwd = true;
   p->fwd_ising = false;
@@ -1369,7 +1371,7 @@ hotrg_status hotrg_forward_device(hotrg_plan p, const double* T0_dev, double* ou
 }
 
 static hotrg_status copy_out(hotrg_plan p, double* lnz, double* log_norms, int* sign) {
-  std::vector<double> h(p->cfg.n_steps + 2);
+  std::vector<double> h(p->n_run + 2);
   CK(cudaMemcpyAsync(h.data(), p->out, sizeof(double) * h.size(), cudaMemcpyDeviceToHost,
                      p->stream));
   hotrg_status r = finish_sync(p);
@@ -1379,7 +1381,7 @@ static hotrg_status copy_out(hotrg_plan p, double* lnz, double* log_norms, int* 
   }
   if (lnz) *lnz = h[0];
   if (sign) *sign = h[1] >= 0 ? 1 : -1;
-  if (log_norms) memcpy(log_norms, h.data() + 2, sizeof(double) * p->cfg.n_steps);
+  if (log_norms) memcpy(log_norms, h.data() + 2, sizeof(double) * p->n_run);
   return HOTRG_OK;
 }
 
@@ -1440,6 +1442,15 @@ hotrg_status hotrg_backward(hotrg_plan p, double* grad, double* dbeta) {
   if (r != HOTRG_OK) return r;
   if (grad) memcpy(grad, h.data(), sizeof(double) * n0);
   if (dbeta) *dbeta = db;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_plan_set_steps(hotrg_plan p, int n_steps) {
+  if (!p) return HOTRG_EINVAL;
+  if (n_steps < 1 || n_steps > p->cfg.n_steps || (p->cfg.w_given && n_steps != p->cfg.n_steps))
+    return fail(p, HOTRG_EINVAL, "steps must be in [1, the plan's n_steps]");
+  if (n_steps != p->n_run) p->have_fwd = p->have_bwd = false;
+  p->n_run = n_steps;
   return HOTRG_OK;
 }
 

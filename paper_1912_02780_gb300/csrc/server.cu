@@ -31,6 +31,10 @@ namespace {
 
 using Clock = std::chrono::steady_clock;
 
+// Depth of the plans the server builds (requests of up to this many steps
+// share them).
+constexpr int kPlanSteps = 40;
+
 struct PlanKey {
   int d_cut, n_steps, want_grad, precision, split_from_step;
   bool operator==(const PlanKey& o) const {
@@ -126,22 +130,36 @@ void worker(hotrg_server_s* s, int slot) {
     res.t_submit = job.t_submit;
     res.slot = slot;
     const hotrg_request& r = job.req;
-    PlanKey key{r.d_cut, r.n_steps, r.want_grad ? 1 : 0, r.precision, r.split_from_step};
+    // Plans are built for kPlanSteps steps (or the request's depth if larger)
+    // and run the request's depth (hotrg_plan_set_steps, bit-identical to a
+    // plan of exactly that depth), so requests of different depths share
+    // plans; where such a plan does not fit the budget, one of the request's
+    // own depth is built.
+    int plan_steps = r.n_steps > kPlanSteps ? r.n_steps : kPlanSteps;
     hotrg_config cfg;
-    hotrg_config_default(&cfg, 2, r.d_cut, r.n_steps);
-    cfg.precision = r.precision;
-    cfg.split_from_step = r.split_from_step > 0 ? r.split_from_step : 1;
-    cfg.want_grad = r.want_grad ? 1 : 0;
-    // forward-only requests take the randomized subspace eigensolver (the
-    // backward's eigensolve adjoint needs all eigenpairs)
-    cfg.eigh_mode = r.want_grad ? 0 : 1;
-    cfg.eigh_power_iters = 2;
-    cfg.eigh_warm_start = r.want_grad ? 0 : 1;
-    // with several slots, the contraction GEMMs leave SMs to the other
-    // requests' latency-bound eigensolver kernels
-    cfg.gemm_sm_reserve = s->caches.size() > 1 ? 16 : 0;
+    auto make_cfg = [&](int nsteps) {
+      hotrg_config_default(&cfg, 2, r.d_cut, nsteps);
+      cfg.precision = r.precision;
+      cfg.split_from_step = r.split_from_step > 0 ? r.split_from_step : 1;
+      cfg.want_grad = r.want_grad ? 1 : 0;
+      // forward-only requests take the randomized subspace eigensolver (the
+      // backward's eigensolve adjoint needs all eigenpairs)
+      cfg.eigh_mode = r.want_grad ? 0 : 1;
+      cfg.eigh_power_iters = 2;
+      cfg.eigh_warm_start = r.want_grad ? 0 : 1;
+      // with several slots, the contraction GEMMs leave SMs to the other
+      // requests' latency-bound eigensolver kernels
+      cfg.gemm_sm_reserve = s->caches.size() > 1 ? 16 : 0;
+    };
+    make_cfg(plan_steps);
     size_t bytes = 0;
     hotrg_status st = hotrg_plan_workspace_bytes(&cfg, &bytes);
+    if (st == HOTRG_OK && bytes > s->budget && plan_steps != r.n_steps) {
+      plan_steps = r.n_steps;
+      make_cfg(plan_steps);
+      st = hotrg_plan_workspace_bytes(&cfg, &bytes);
+    }
+    PlanKey key{r.d_cut, plan_steps, r.want_grad ? 1 : 0, r.precision, r.split_from_step};
     hotrg_plan plan = nullptr;
     auto& cache = s->caches[slot];
     for (auto it = cache.begin(); it != cache.end(); ++it) {
@@ -183,6 +201,7 @@ void worker(hotrg_server_s* s, int slot) {
     }
     res.t_start = s->now();
     lk.unlock();
+    if (st == HOTRG_OK) st = hotrg_plan_set_steps(plan, r.n_steps);
     if (st == HOTRG_OK) {
       st = hotrg_forward_ising(plan, r.beta, r.J, r.h, &res.lnz_per_site, nullptr, nullptr);
       if (st == HOTRG_OK && r.want_grad) st = hotrg_backward(plan, nullptr, &res.dlnz_dbeta);

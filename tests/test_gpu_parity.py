@@ -371,3 +371,22 @@ def test_sm_reserve_does_not_change_results():
     for o in out[1:]:
         assert o[0] == out[0][0]
         assert np.array_equal(o[1], out[0][1]) and np.array_equal(o[2], out[0][2])
+
+
+def test_plan_set_steps_equals_plan_of_that_depth():
+    """A plan run for fewer steps than it was created with gives the result
+    of a plan of exactly that depth, bit for bit, forward and backward (the
+    server shares one plan among requests of different depths)."""
+    beta, h = 0.43, 0.02
+    with hot.Plan(2, 16, 9, "bf16x6", split_from_step=4) as p:
+        lnz9, ln9, _ = p.forward_ising(beta, 1.0, h)
+        g9, db9 = p.backward(want_dbeta=True)
+    with hot.Plan(2, 16, 14, "bf16x6", split_from_step=4) as p:
+        p.set_steps(9)
+        lnz, ln, _ = p.forward_ising(beta, 1.0, h)
+        g, db = p.backward(want_dbeta=True)
+        p.set_steps(14)
+        lnz14, ln14, _ = p.forward_ising(beta, 1.0, h)
+    assert lnz == lnz9 and np.array_equal(ln, ln9)
+    assert np.array_equal(g, g9) and db == db9
+    assert len(ln14) == 14 and np.array_equal(ln14[:9], ln9)
