@@ -228,6 +228,11 @@ hotrg_status hotrg_backward_device(hotrg_plan plan, double* grad_dev);
  * diagnostics keep the plan's length, with entries past n_steps stale. */
 hotrg_status hotrg_plan_set_steps(hotrg_plan plan, int n_steps);
 
+/* Bind the plan to another CUDA stream (NULL = legacy default stream): waits
+ * for the plan's work on its current stream, then enqueues everything on the
+ * new one. */
+hotrg_status hotrg_plan_set_stream(hotrg_plan plan, void* cuda_stream);
+
 /* Wait for the plan's stream and report any device-side failure. */
 hotrg_status hotrg_sync(hotrg_plan plan);
 
@@ -264,11 +269,13 @@ hotrg_status hotrg_device_supports_split(void);
  * stream on the device current at hotrg_server_create, so requests that arrive
  * while others are on the GPU start as soon as a slot and device memory are
  * free and their kernels overlap on the device.  Every live plan is charged
- * its hotrg_plan_workspace_bytes against hbm_budget_bytes; slots keep built
- * plans for reuse by later requests of the same D_cut, precision and gradient
- * need (plans are built for 40 steps, or the request's depth if larger or if
- * a 40-step plan would not fit the budget, and run each request's own depth)
- * and free idle ones when a new plan would not fit.  A request whose plan alone exceeds the budget
+ * its hotrg_plan_workspace_bytes against hbm_budget_bytes; built plans stay in
+ * one pool shared by all slots for reuse by later requests of the same D_cut,
+ * precision and gradient need (plans are built for 40 steps, or the request's
+ * depth if larger or if a 40-step plan would not fit the budget, and run each
+ * request's own depth); idle ones are freed, coldest first, when a new plan
+ * would not fit, and a slot waits for a running request's plan when all
+ * pooled plans are in use.  A request whose plan alone exceeds the budget
  * finishes with status HOTRG_ENOMEM.  Requests without gradients use the
  * randomized subspace eigensolver (eigh_mode 1, 2 power iterations).  Times are seconds since the server was
  * created.  Submit, poll, wait, drain and stats are thread-safe. */

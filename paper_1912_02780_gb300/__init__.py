@@ -31,7 +31,7 @@ EXPORTS = (
     "hotrg_isometries", "hotrg_set_isometries", "hotrg_isometry_adjoints", "hotrg_mera_update", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
-    "hotrg_plan_set_steps",
+    "hotrg_plan_set_steps", "hotrg_plan_set_stream",
     "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
@@ -114,6 +114,7 @@ def lib() -> ctypes.CDLL:
     L.hotrg_backward_device.argtypes = [vp, vp]
     L.hotrg_sync.argtypes = [vp]
     L.hotrg_plan_set_steps.argtypes = [vp, ctypes.c_int]
+    L.hotrg_plan_set_stream.argtypes = [vp, vp]
     L.hotrg_diagnostics.argtypes = [vp, _dp, _dp, _ip]
     L.hotrg_step_dims.argtypes = [vp, ctypes.c_int, _ip, _ip, _ip]
     L.hotrg_eigh_diagnostics.argtypes = [vp, _dp, _ip, _ip, ctypes.POINTER(ctypes.c_longlong)]

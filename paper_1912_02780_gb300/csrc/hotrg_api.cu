@@ -1445,6 +1445,17 @@ hotrg_status hotrg_backward(hotrg_plan p, double* grad, double* dbeta) {
   return HOTRG_OK;
 }
 
+hotrg_status hotrg_plan_set_stream(hotrg_plan p, void* cuda_stream) {
+  if (!p) return HOTRG_EINVAL;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(cuda_stream);
+  if (s == p->stream) return HOTRG_OK;
+  CK(cudaStreamSynchronize(p->stream));   // the plan's work on its old stream is done
+  if (cusolverDnSetStream(p->solver, s) != CUSOLVER_STATUS_SUCCESS)
+    return fail(p, HOTRG_ECUDA, "cusolverDnSetStream failed");
+  p->stream = s;
+  return HOTRG_OK;
+}
+
 hotrg_status hotrg_plan_set_steps(hotrg_plan p, int n_steps) {
   if (!p) return HOTRG_EINVAL;
   if (n_steps < 1 || n_steps > p->cfg.n_steps || (p->cfg.w_given && n_steps != p->cfg.n_steps))

@@ -8,11 +8,12 @@
 // slot's FP64 eigensolve overlaps another's tensor-core contractions).
 //
 // Admission by device memory: every live plan is charged its
-// hotrg_plan_workspace_bytes against the budget.  A slot keeps the plans it
-// has built (LRU) for reuse by later requests of the same shape; before a new
-// plan is built the slot frees its own idle plans, and if that is not enough
-// it asks the other slots to free their idle plans and waits for memory.  A
-// request that could never fit the budget is rejected with HOTRG_ENOMEM.
+// hotrg_plan_workspace_bytes against the budget.  Built plans stay in one pool
+// shared by all slots (LRU); a slot takes an idle plan of its request's shape
+// (re-bound to the slot's stream) or builds one, first freeing idle plans from
+// the cold end of the pool and, if the plans in use still leave no room,
+// waiting until a running request returns its plan.  A request that could
+// never fit the budget is rejected with HOTRG_ENOMEM.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -43,10 +44,11 @@ struct PlanKey {
   }
 };
 
-struct CachedPlan {
+struct PooledPlan {
   PlanKey key;
   hotrg_plan plan;
   size_t bytes;
+  bool in_use;
 };
 
 struct Job {
@@ -65,12 +67,12 @@ struct hotrg_server_s {
   std::deque<Job> queue;
   std::unordered_map<uint64_t, hotrg_result> results;
   std::vector<std::thread> workers;
-  std::vector<std::list<CachedPlan>> caches;   // per slot, front = most recent
+  std::list<PooledPlan> pool;   // built plans of all slots, front = most recently used
+  int slots = 0;
   std::vector<int> busy;
   size_t bytes_in_use = 0, peak_bytes = 0;
   uint64_t next_ticket = 1, submitted = 0, completed = 0, failed = 0, created = 0, evicted = 0;
   uint64_t admission_waits = 0;   // requests that had to wait for device memory
-  int trim_epoch = 0;
   int running = 0;
   bool stop = false;
   Clock::time_point t0;
@@ -80,41 +82,42 @@ struct hotrg_server_s {
 
 namespace {
 
-void free_plan(hotrg_server_s* s, CachedPlan& cp) {
-  hotrg_plan_destroy(cp.plan);
-  s->bytes_in_use -= cp.bytes;
-  s->evicted += 1;
+// Called with the lock held: an idle pooled plan of this key, marked in use
+// and moved to the warm end of the pool, or nullptr.
+hotrg_plan take_idle(hotrg_server_s* s, const PlanKey& key) {
+  for (auto it = s->pool.begin(); it != s->pool.end(); ++it) {
+    if (!it->in_use && it->key == key) {
+      it->in_use = true;
+      s->pool.splice(s->pool.begin(), s->pool, it);
+      return s->pool.front().plan;
+    }
+  }
+  return nullptr;
 }
 
-// Called with the lock held: drop this slot's idle cached plans (LRU first)
-// until `need` more bytes fit, or all are gone.
-void trim_own(hotrg_server_s* s, int slot, size_t need, std::unique_lock<std::mutex>& lk) {
-  auto& c = s->caches[slot];
-  while (!c.empty() && s->bytes_in_use + need > s->budget) {
-    CachedPlan cp = c.back();
-    c.pop_back();
-    lk.unlock();
-    hotrg_plan_destroy(cp.plan);
-    lk.lock();
-    s->bytes_in_use -= cp.bytes;
+// Called with the lock held: free the coldest idle plan; false if none is idle.
+bool evict_one(hotrg_server_s* s, std::unique_lock<std::mutex>& lk) {
+  for (auto it = s->pool.end(); it != s->pool.begin();) {
+    --it;
+    if (it->in_use) continue;
+    PooledPlan pp = *it;
+    s->pool.erase(it);
+    s->bytes_in_use -= pp.bytes;
     s->evicted += 1;
+    lk.unlock();
+    hotrg_plan_destroy(pp.plan);
+    lk.lock();
+    return true;
   }
+  return false;
 }
 
 void worker(hotrg_server_s* s, int slot) {
   cudaSetDevice(s->device);
   cudaStream_t stream = nullptr;
   cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
-  int seen_trim = 0;
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
-    // idle: honour trim requests from slots waiting for memory
-    if (seen_trim != s->trim_epoch) {
-      seen_trim = s->trim_epoch;
-      trim_own(s, slot, s->budget + 1, lk);
-      s->cv.notify_all();
-      continue;
-    }
     if (s->stop && s->queue.empty()) break;
     if (s->queue.empty()) {
       s->cv.wait(lk);
@@ -149,7 +152,7 @@ void worker(hotrg_server_s* s, int slot) {
       cfg.eigh_warm_start = r.want_grad ? 0 : 1;
       // with several slots, the contraction GEMMs leave SMs to the other
       // requests' latency-bound eigensolver kernels
-      cfg.gemm_sm_reserve = s->caches.size() > 1 ? 16 : 0;
+      cfg.gemm_sm_reserve = s->slots > 1 ? 16 : 0;
     };
     make_cfg(plan_steps);
     size_t bytes = 0;
@@ -161,52 +164,54 @@ void worker(hotrg_server_s* s, int slot) {
     }
     PlanKey key{r.d_cut, plan_steps, r.want_grad ? 1 : 0, r.precision, r.split_from_step};
     hotrg_plan plan = nullptr;
-    auto& cache = s->caches[slot];
-    for (auto it = cache.begin(); it != cache.end(); ++it) {
-      if (it->key == key) {
-        CachedPlan cp = *it;
-        cache.erase(it);
-        cache.push_front(cp);
-        plan = cp.plan;
-        break;
-      }
-    }
+    if (st == HOTRG_OK) plan = take_idle(s, key);
     if (st == HOTRG_OK && !plan) {
       if (bytes > s->budget) {
         st = HOTRG_ENOMEM;
       } else {
-        trim_own(s, slot, bytes, lk);
-        if (s->bytes_in_use + bytes > s->budget) s->admission_waits += 1;
-        while (s->bytes_in_use + bytes > s->budget) {
-          // ask idle slots to free their cached plans, then wait for memory
-          s->trim_epoch += 1;
-          seen_trim = s->trim_epoch;
-          s->cv.notify_all();
-          s->cv.wait_for(lk, std::chrono::milliseconds(50));
-          trim_own(s, slot, bytes, lk);
+        bool waited = false;
+        while (!plan && s->bytes_in_use + bytes > s->budget) {
+          if (evict_one(s, lk)) {
+            plan = take_idle(s, key);   // another slot may have returned one meanwhile
+            continue;
+          }
+          // every pooled plan is in use: wait for one to come back
+          if (!waited) {
+            s->admission_waits += 1;
+            waited = true;
+          }
+          s->cv.wait(lk);
+          plan = take_idle(s, key);
         }
-        s->bytes_in_use += bytes;
-        s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
-        lk.unlock();
-        st = hotrg_plan_create(&cfg, stream, &plan);
-        lk.lock();
-        if (st == HOTRG_OK) {
-          s->created += 1;
-          cache.push_front(CachedPlan{key, plan, bytes});
-        } else {
-          s->bytes_in_use -= bytes;
-          plan = nullptr;
+        if (!plan) {
+          s->bytes_in_use += bytes;
+          s->peak_bytes = std::max(s->peak_bytes, s->bytes_in_use);
+          lk.unlock();
+          st = hotrg_plan_create(&cfg, stream, &plan);
+          lk.lock();
+          if (st == HOTRG_OK) {
+            s->created += 1;
+            s->pool.push_front(PooledPlan{key, plan, bytes, true});
+          } else {
+            s->bytes_in_use -= bytes;
+            plan = nullptr;
+            s->cv.notify_all();
+          }
         }
       }
     }
     res.t_start = s->now();
     lk.unlock();
+    if (st == HOTRG_OK) st = hotrg_plan_set_stream(plan, stream);
     if (st == HOTRG_OK) st = hotrg_plan_set_steps(plan, r.n_steps);
     if (st == HOTRG_OK) {
       st = hotrg_forward_ising(plan, r.beta, r.J, r.h, &res.lnz_per_site, nullptr, nullptr);
       if (st == HOTRG_OK && r.want_grad) st = hotrg_backward(plan, nullptr, &res.dlnz_dbeta);
     }
     lk.lock();
+    if (plan)
+      for (auto& pp : s->pool)
+        if (pp.plan == plan) pp.in_use = false;
     res.status = st;
     res.t_finish = s->now();
     s->results[job.ticket] = res;
@@ -216,8 +221,6 @@ void worker(hotrg_server_s* s, int slot) {
     if (st != HOTRG_OK) s->failed += 1;
     s->cv.notify_all();
   }
-  for (auto& cp : s->caches[slot]) free_plan(s, cp);
-  s->caches[slot].clear();
   lk.unlock();
   cudaStreamSynchronize(stream);
   cudaStreamDestroy(stream);
@@ -237,7 +240,7 @@ hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_s
   }
   s->budget = hbm_budget_bytes;
   s->t0 = Clock::now();
-  s->caches.resize(max_slots);
+  s->slots = max_slots;
   s->busy.assign(max_slots, 0);
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s, i);
   *out = s;
@@ -309,6 +312,7 @@ void hotrg_server_destroy(hotrg_server s) {
     s->cv.notify_all();
   }
   for (auto& t : s->workers) t.join();
+  for (auto& pp : s->pool) hotrg_plan_destroy(pp.plan);   // waits for each plan's stream
   delete s;
 }
 
