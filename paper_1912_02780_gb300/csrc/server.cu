@@ -68,6 +68,8 @@ struct hotrg_server_s {
   std::unordered_map<uint64_t, hotrg_result> results;
   std::vector<std::thread> workers;
   std::list<PooledPlan> pool;   // built plans of all slots, front = most recently used
+  std::vector<cudaStream_t> streams;   // one per slot; owned by the server, destroyed after
+                                       // every pooled plan (plans keep a stream handle)
   int slots = 0;
   std::vector<int> busy;
   size_t bytes_in_use = 0, peak_bytes = 0;
@@ -114,8 +116,7 @@ bool evict_one(hotrg_server_s* s, std::unique_lock<std::mutex>& lk) {
 
 void worker(hotrg_server_s* s, int slot) {
   cudaSetDevice(s->device);
-  cudaStream_t stream = nullptr;
-  cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking);
+  cudaStream_t stream = s->streams[slot];
   std::unique_lock<std::mutex> lk(s->mu);
   while (true) {
     if (s->stop && s->queue.empty()) break;
@@ -223,7 +224,6 @@ void worker(hotrg_server_s* s, int slot) {
   }
   lk.unlock();
   cudaStreamSynchronize(stream);
-  cudaStreamDestroy(stream);
 }
 
 }  // namespace
@@ -242,6 +242,15 @@ hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_s
   s->t0 = Clock::now();
   s->slots = max_slots;
   s->busy.assign(max_slots, 0);
+  s->streams.assign(max_slots, nullptr);
+  for (int i = 0; i < max_slots; ++i) {
+    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
+      delete s;
+      return HOTRG_ECUDA;
+    }
+  }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s, i);
   *out = s;
   return HOTRG_OK;
@@ -312,7 +321,11 @@ void hotrg_server_destroy(hotrg_server s) {
     s->cv.notify_all();
   }
   for (auto& t : s->workers) t.join();
-  for (auto& pp : s->pool) hotrg_plan_destroy(pp.plan);   // waits for each plan's stream
+  // plans first (each waits for its stream), then the streams they were bound to
+  for (auto& pp : s->pool) hotrg_plan_destroy(pp.plan);
+  s->pool.clear();
+  for (cudaStream_t st : s->streams)
+    if (st) cudaStreamDestroy(st);
   delete s;
 }
 
