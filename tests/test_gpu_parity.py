@@ -390,3 +390,40 @@ def test_plan_set_steps_equals_plan_of_that_depth():
     assert lnz == lnz9 and np.array_equal(ln, ln9)
     assert np.array_equal(g, g9) and db == db9
     assert len(ln14) == 14 and np.array_equal(ln14[:9], ln9)
+
+
+@pytest.mark.parametrize("name,h", [("c3_bc_h0_grad", 0.0), ("c3_bc_h001_grad", 0.01)])
+def test_backward_split_c3_ising_critical_d64_against_stored_oracle(name, h):
+    """C3 at full size: Ising at beta_c, D_cut = 64, 40 steps, split precision
+    (FP64 steps 1-6, four planes on 7-8, three after), the full backward with
+    per-step recomputation of the stage contractions from the stored T_{k-1}
+    and w_k, against the oracle's stored d(ln Z/N)/d T0 (all 16 entries) and
+    d(ln Z/N)/d beta (tests/golden/make_golden.py c3_bc_h0_grad /
+    c3_bc_h001_grad).  The Euler identity <T0, g> = 1 holds for any
+    truncation.  With h = 0.01 the relative cut gap falls to 3e-21 at
+    steps 13-17 (oracle record): the gradient through the truncated eigensolve
+    is then not determined by the input (SURVEY c-4 / c-9 reading: flagged, not
+    a parity failure), so that case asserts ln Z/N, the Euler identity and the
+    beta derivative only loosely and reports the rest."""
+    g = _golden(name)
+    with hot.Plan(2, 64, 40, "bf16x6", split_from_step=7, hi_precision_steps=2) as p:
+        lnz, _, sign = p.forward_ising(synth.BETA_C, 1.0, h)
+        grad, db = p.backward(want_dbeta=True)
+        _, gap, _ = p.diagnostics()
+    g_ref = np.array(g["dlnz_dT0"]).reshape(2, 2, 2, 2)
+    err_g = np.max(np.abs(grad - g_ref)) / np.max(np.abs(g_ref))
+    err_b = abs(db - g["dlnz_dbeta"]) / abs(g["dlnz_dbeta"])
+    T0 = ising.ising_T0(synth.BETA_C, 1.0, h)
+    euler = np.sum(grad * T0)
+    min_gap = min(x for x in g["cut_gap"] if x is not None)
+    print(f"{name}: |df| = {abs(lnz - g['lnz']) / synth.BETA_C:.2e}, grad rel err {err_g:.2e}, "
+          f"dbeta rel err {err_b:.2e}, euler - 1 = {euler - 1:.2e}, min cut gap (oracle) "
+          f"{min_gap:.1e}, (GPU) {np.nanmin(gap[gap > 0]):.1e}")
+    assert sign == g["trace_sign"]
+    assert abs(lnz - g["lnz"]) / synth.BETA_C < 1e-9
+    assert abs(euler - 1.0) < 1e-6
+    if min_gap > 1e-12:
+        assert err_g < 1e-6
+        assert err_b < 1e-6
+    else:
+        assert err_b < 1e-3
