@@ -426,14 +426,16 @@ def run_grid(args):
     t0 = time.perf_counter()
     res = ising_thermodynamics(betas, 32, 30, args.precision,
                                split_from_step=args.split_from if split else 1,
-                               hi_precision_steps=args.hi_steps)
+                               hi_precision_steps=args.hi_steps, concurrent=args.concurrent,
+                               sm_reserve=args.sm_reserve)
     dt = time.perf_counter() - t0
     line = {"metric": "beta-grid solves/s (forward + backward)", "value": len(betas) / dt,
             "unit": "solves/s", "higher_is_better": True, "seconds": dt,
             "dtype": args.precision, "data": "synthetic",
             "config": {"workload": "c2_grid", "betas": len(betas), "d_cut": 32, "n_steps": 30,
                        "split_from_step": args.split_from if split else None,
-                       "hi_precision_steps": args.hi_steps if split else None}}
+                       "hi_precision_steps": args.hi_steps if split else None,
+                       "concurrent_plans": args.concurrent, "sm_reserve": args.sm_reserve}}
     g = golden("c2_grid")
     if g:
         lnz_ref = np.array([q["lnz"] for q in g["points"]])

@@ -34,16 +34,51 @@ def grid_derivative(x: np.ndarray, y: np.ndarray) -> np.ndarray:
 
 def ising_thermodynamics(betas, d_cut: int, n_steps: int, precision: str = "fp64",
                          split_from_step: int = 1, J: float = 1.0, h: float = 0.0,
-                         hi_precision_steps: int = 2) -> dict:
-    """ln Z / N, f, u and c on a beta grid (one plan reused for every beta)."""
+                         hi_precision_steps: int = 2, concurrent: int = 1,
+                         sm_reserve: int = 0) -> dict:
+    """ln Z / N, f, u and c on a beta grid.  ``concurrent`` plans, each on its
+    own CUDA stream and host thread, take the betas round-robin (so that one
+    solve's latency-bound eigensolver kernels run beside another's
+    contractions; ``sm_reserve`` SMs are left free by each plan's
+    contraction GEMMs for that); every beta's result is the same as with one
+    plan."""
+    import threading
     betas = np.asarray(betas, dtype=np.float64)
     lnz = np.empty_like(betas)
     dlnz = np.empty_like(betas)
-    with Plan(2, d_cut, n_steps, precision, split_from_step=split_from_step, want_grad=True,
-              hi_precision_steps=hi_precision_steps) as p:
-        for i, b in enumerate(betas):
-            lnz[i], _, _ = p.forward_ising(float(b), J, h)
-            _, dlnz[i] = p.backward(want_dbeta=True)
+    C = max(1, min(int(concurrent), len(betas)))
+    streams = []
+    if C > 1:
+        import torch
+        streams = [torch.cuda.Stream() for _ in range(C)]
+    plans = [Plan(2, d_cut, n_steps, precision, split_from_step=split_from_step, want_grad=True,
+                  hi_precision_steps=hi_precision_steps,
+                  stream=streams[c].cuda_stream if streams else None,
+                  gemm_sm_reserve=sm_reserve if C > 1 else 0) for c in range(C)]
+    errors = []
+
+    def run(c):
+        try:
+            for i in range(c, len(betas), C):
+                lnz[i], _, _ = plans[c].forward_ising(float(betas[i]), J, h)
+                _, dlnz[i] = plans[c].backward(want_dbeta=True)
+        except Exception as e:          # re-raised in the caller's thread
+            errors.append(e)
+
+    try:
+        if C == 1:
+            run(0)
+        else:
+            threads = [threading.Thread(target=run, args=(c,)) for c in range(C)]
+            for t in threads:
+                t.start()
+            for t in threads:
+                t.join()
+    finally:
+        for p in plans:
+            p.close()
+    if errors:
+        raise errors[0]
     u = -dlnz
     c = -betas ** 2 * grid_derivative(betas, u) if len(betas) >= 3 else np.full_like(betas, np.nan)
     return dict(beta=betas, lnz=lnz, f=-lnz / betas, u=u, c=c)

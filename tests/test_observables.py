@@ -90,3 +90,15 @@ def test_ising_grid_fp64_and_specific_heat_against_stored_oracle():
     assert du.max() < 1e-6
     assert dc.max() < 1e-6
     assert np.all(c > 0)
+
+
+@pytest.mark.gpu
+def test_ising_grid_concurrent_plans_equal_single_plan():
+    """Several plans on their own streams (the grid's concurrent mode) give
+    every beta the same result as one plan, bit for bit."""
+    from paper_1912_02780_gb300.observables import ising_thermodynamics
+    betas = np.linspace(0.40, 0.46, 6)
+    a = ising_thermodynamics(betas, 16, 16, "bf16x6", split_from_step=5)
+    b = ising_thermodynamics(betas, 16, 16, "bf16x6", split_from_step=5, concurrent=3,
+                             sm_reserve=16)
+    assert np.array_equal(a["lnz"], b["lnz"]) and np.array_equal(a["u"], b["u"])
