@@ -450,6 +450,32 @@ def run_grid(args):
     print(json.dumps(line), flush=True)
 
 
+def run_dtrg_study(args):
+    """Accuracy study of differentiable TRG near T_c (the shape of main text
+    Fig. 2): Ising, D_cut = 24, 30 steps, split precision; HOTRG and dTRG
+    (MERA updates with n_inner = 5 per layer, sweeps over the layers until a
+    sweep changes ln Z/N by at most 1e-4 of the total improvement, at most
+    --study-sweeps) free energies against Onsager on a beta scan across T_c."""
+    from oracle import exact
+    from paper_1912_02780_gb300.dtrg import dtrg_sweeps
+    betas = [float(b) for b in args.study_betas.split(",")]
+    rows = []
+    for b in betas:
+        t0 = time.perf_counter()
+        r = dtrg_sweeps(2, 24, 30, n_sweeps=args.study_sweeps, n_inner=5, beta=b,
+                        precision="bf16x6", split_from_step=5, tol=1e-4)
+        ons = exact.onsager_lnz(b)
+        row = {"beta": b, "rel_err_f_hotrg": abs(r["lnz_hotrg"] - ons) / abs(ons),
+               "rel_err_f_dtrg": abs(r["lnz_final"] - ons) / abs(ons), "sweeps": r["sweeps"],
+               "lnz_per_sweep": r["lnz"], "seconds": time.perf_counter() - t0}
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    print(json.dumps({"metric": "dTRG vs HOTRG free-energy error near T_c",
+                      "config": {"model": "ising", "d_cut": 24, "n_steps": 30, "n_inner": 5,
+                                 "tol": 1e-4, "precision": "bf16x6", "split_from_step": 5},
+                      "rows": rows}), flush=True)
+
+
 def run_dtrg(args):
     """Differentiable-TRG MERA updates at the workload's size: start from the
     HOTRG isometries, then time --steps updates (each a forward with the
@@ -541,6 +567,10 @@ def main():
                     help="the Ising beta grid (64 betas, D_cut = 32): f, u, c and solves/s")
     ap.add_argument("--dtrg", action="store_true",
                     help="time differentiable-TRG MERA updates at the workload's size")
+    ap.add_argument("--dtrg-study", action="store_true",
+                    help="dTRG vs HOTRG free-energy errors against Onsager near T_c (D_cut = 24)")
+    ap.add_argument("--study-betas", default="0.40,0.42,0.43,0.4406867935097715,0.45,0.46,0.48")
+    ap.add_argument("--study-sweeps", type=int, default=8)
     ap.add_argument("--gemm-case", default="",
                     help="M,N,K: one three-plane split GEMM of the stage-2 kind through the "
                          "kernel-check entry point (a small case for ncu captures)")
@@ -561,6 +591,8 @@ def main():
         return run_grid(args)
     if args.dtrg:
         return run_dtrg(args)
+    if args.dtrg_study:
+        return run_dtrg_study(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
