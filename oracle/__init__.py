@@ -17,6 +17,14 @@ hotrg      plain NumPy/LAPACK HOTRG forward (SM Sec. B, HOTRG step equation;
            of the environment Gram matrix) and its reverse-mode backward
            (SM Sec. B second-renormalization recursion, SM Sec. E Jacobian
            and chain rule, plus the adjoint of the truncated eigensolve).
+dtrg       differentiable-TRG sweeps: environments of the isometries and
+           the MERA update (main text Eq. (1) and the MERA paragraph).
+xy         quantum XY chain: exact partition functions (SM Sec. G, with
+           exact diagonalisation as their pin) and the second-order
+           Trotter MPO of rho(tau) (SM Sec. F).
+xtrg       scheme (b) of main text Fig. 1b: vertical-only coarse-graining
+           of the MPO (exponential cooling), the exact final product, its
+           backward and the differentiable-TRG cooling with depth n_d.
 exact      closed forms and exact small-lattice references used as pins:
            Onsager's free energy (two independent integral forms), brute-force
            enumeration of periodic tori (C), and exact transfer-matrix
