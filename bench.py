@@ -520,6 +520,91 @@ def run_dtrg(args):
     print(json.dumps(line), flush=True)
 
 
+def run_xy(args):
+    """Scheme (b) on the infinite quantum XY chain, the workload of main text
+    Fig. 3b: cool rho(tau), tau = 12.8 / 2^18 (second-order Trotter MPO), by
+    17 doublings to beta = 12.8 (the exact final product doubles once more),
+    per D_cut: plain scheme (b) and differentiable TRG with depth n_d (MERA
+    updates of the newest layers against the free energy at the current
+    temperature), wall time of the whole cooling and the free-energy error
+    against the exact Jordan-Wigner solution."""
+    import torch
+    from oracle import xtrg as oxtrg
+    from oracle import xy as oxy
+    from paper_1912_02780_gb300 import xtrg as gx
+    tau, n = 12.8 / 2 ** 18, 17
+    beta_end = tau * 2 ** (n + 1)
+    f_ex = -oxy.lnz_exact_infinite(beta_end) / beta_end
+    ds = [int(x) for x in args.xy_d.split(",")]
+    kw = dict(eigh_mode=1, eigh_power_iters=2)
+    gx.cooling(tau, ds[0], 4, **kw)                      # warm-up (library load, first plans)
+    rows = []
+    for D in ds:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        plain = gx.cooling(tau, D, n, **kw)
+        t_plain = time.perf_counter() - t0
+        row = {"d_cut": D, "seconds_plain": t_plain,
+               "rel_err_f_plain": abs(plain["f"][-1] - f_ex) / abs(f_ex)}
+        if args.xy_nd > 0:
+            t0 = time.perf_counter()
+            opt = gx.cooling(tau, D, n, n_d=args.xy_nd, n_sweeps=args.xy_sweeps,
+                             n_inner=args.xy_inner, **kw)
+            row["seconds_dtrg"] = time.perf_counter() - t0
+            row["rel_err_f_dtrg"] = abs(opt["f"][-1] - f_ex) / abs(f_ex)
+        rows.append(row)
+        print(json.dumps(row), flush=True)
+    cpu = None
+    if not args.no_cpu_baseline:
+        Dc = ds[0]
+        t0 = time.perf_counter()
+        oxtrg.xtrg_forward(oxy.mpo_cell(tau), Dc, n)
+        cpu = {"d_cut": Dc, "seconds_plain": time.perf_counter() - t0, "cores": os.cpu_count(),
+               "kind": "oracle", "sample": f"plain scheme (b) cooling at D_cut = {Dc}"}
+    fit = None
+    big = [r for r in rows if r["d_cut"] >= 32]
+    if len(big) >= 2:
+        x = np.log([r["d_cut"] for r in big])
+        y = np.log([r["seconds_plain"] for r in big])
+        fit = float(np.polyfit(x, y, 1)[0])
+    print(json.dumps({"metric": "XY-chain cooling to beta = 12.8, seconds per run",
+                      "config": {"workload": "infinite XY chain, second-order Trotter MPO",
+                                 "tau": tau, "doublings": n, "beta": beta_end,
+                                 "dtrg": {"n_d": args.xy_nd, "n_sweeps": args.xy_sweeps,
+                                          "n_inner": args.xy_inner},
+                                 "eigensolver": "randomized subspace (2 power iterations, guard)",
+                                 "precision": "fp64"},
+                      "f_exact": f_ex, "rows": rows, "gamma_plain_fit_D>=32": fit,
+                      "cpu_baseline": cpu}), flush=True)
+
+
+def run_lbfgs(args):
+    """L-BFGS optimisation of the isometries (SM Sec. D) against the MERA
+    update: one sweep over the layers of the Ising network at beta = 0.40,
+    D_cut = --lbfgs-d, 20 steps, FP64; wall time and the gain in ln Z/N
+    against Onsager for each."""
+    import torch
+    from oracle import exact
+    from paper_1912_02780_gb300 import dtrg as gd
+    beta, D, n = 0.40, args.lbfgs_d, 20
+    ons = exact.onsager_lnz(beta)
+    gd.lbfgs_sweeps(2, D, 6, n_sweeps=1, n_iter=2, beta=beta)          # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    lb = gd.lbfgs_sweeps(2, D, n, n_sweeps=1, n_iter=args.lbfgs_iters, beta=beta)
+    t_lb = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    me = gd.dtrg_sweeps(2, D, n, n_sweeps=1, n_inner=args.lbfgs_iters, beta=beta)
+    t_me = time.perf_counter() - t0
+    print(json.dumps({"metric": "isometry optimisation, one sweep",
+                      "config": {"model": "ising", "beta": beta, "d_cut": D, "n_steps": n,
+                                 "iterations_per_layer": args.lbfgs_iters, "precision": "fp64"},
+                      "lbfgs": {"seconds": t_lb, "evaluations": lb["evals"],
+                                "abs_err_lnz": abs(lb["lnz"][-1] - ons)},
+                      "mera": {"seconds": t_me, "abs_err_lnz": abs(me["lnz_final"] - ons)},
+                      "hotrg_abs_err_lnz": abs(lb["lnz_hotrg"] - ons)}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -571,6 +656,16 @@ def main():
                     help="dTRG vs HOTRG free-energy errors against Onsager near T_c (D_cut = 24)")
     ap.add_argument("--study-betas", default="0.40,0.42,0.43,0.4406867935097715,0.45,0.46,0.48")
     ap.add_argument("--study-sweeps", type=int, default=8)
+    ap.add_argument("--xy", action="store_true",
+                    help="scheme (b): XY-chain cooling to beta = 12.8, seconds per D_cut")
+    ap.add_argument("--xy-d", default="16,32,64,96,128")
+    ap.add_argument("--xy-nd", type=int, default=1, help="dTRG depth (0: plain only)")
+    ap.add_argument("--xy-sweeps", type=int, default=1)
+    ap.add_argument("--xy-inner", type=int, default=5)
+    ap.add_argument("--lbfgs", action="store_true",
+                    help="L-BFGS (exponential parametrisation) vs MERA update, one sweep")
+    ap.add_argument("--lbfgs-d", type=int, default=16)
+    ap.add_argument("--lbfgs-iters", type=int, default=5)
     ap.add_argument("--gemm-case", default="",
                     help="M,N,K: one three-plane split GEMM of the stage-2 kind through the "
                          "kernel-check entry point (a small case for ncu captures)")
@@ -593,6 +688,10 @@ def main():
         return run_dtrg(args)
     if args.dtrg_study:
         return run_dtrg_study(args)
+    if args.xy:
+        return run_xy(args)
+    if args.lbfgs:
+        return run_lbfgs(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

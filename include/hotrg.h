@@ -140,6 +140,27 @@ typedef struct {
                                fixed point of the flow) and run this many power iterations
                                there instead of eigh_power_iters; the accuracy guard still
                                checks every step.  0 = off (default), at most 16.          */
+  int scheme;               /* 0 = scheme (a) of main text Fig. 1a (default): steps alternate
+                               direction and the last tensor is traced as a torus.
+                               1 = scheme (b) of Fig. 1b: vertical merges only (the MPO
+                               product rho(2 tau) = rho(tau) rho(tau) for a density matrix,
+                               SM Sec. F): no re-orientation, the vertical (physical) legs keep
+                               dimension d0 and the horizontal bond grows to D' = min(X^2,
+                               d_cut); T0 is the cell tensor of a translation-invariant chain.
+                               The remaining one-dimensional structure is contracted exactly:
+                               the free energy of the depth-n chain is evaluated as
+                               Tr[rho rho] of two copies of it on the infinite chain,
+                                 lnz = sum_k ln c_k / 2^k + ln lambda_max(A_n) / 2^(n+1),
+                                 (A V)[x1][x2] = sum_{y,j} T~_n[x1][x1'][y][j] V[x1'][x2']
+                                                 T~_n[x2][x2'][j][y],
+                               lambda_max the dominant eigenvalue of that cell transfer
+                               operator (FP64 power iteration; HOTRG_ENOTCONV if it has no
+                               simple positive dominant eigenvalue).  lnz is ln Z per copy of
+                               T0 in the 2^(n+1)-deep network: ln Tr rho(2^(n+1) tau) per cell
+                               is 2^(n+1) lnz.  d_cut <= 4096.                             */
+  int chain_steps;          /* scheme 1: 1 = also evaluate lnz of every depth k < n during the
+                               forward (hotrg_chain_lnz_steps: the whole cooling curve, beta_k
+                               = 2^(k+1) tau, from one forward); 0 = the last depth only.  */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -148,7 +169,8 @@ typedef struct hotrg_plan_s* hotrg_plan;
  * fixed_w_grad = 0, eigh_broadening = 1e-12, gram_split_from_step = 0,
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
  * epilogue_split = 1, split_chunk_elems = 0, w_given = 0, eigh_residual_tol = 0,
- * stage2_n_group = 0, stage2_pair = 0, gemm_sm_reserve = 0, eigh_warm_start = 0.
+ * stage2_n_group = 0, stage2_pair = 0, gemm_sm_reserve = 0, eigh_warm_start = 0,
+ * scheme = 0, chain_steps = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
@@ -170,10 +192,53 @@ void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
  *   FP64), w_k = U V^T.  The next forward sees the new w_k.
  * HOTRG_ESTATE when called out of order (no forward / backward yet, or a plan
  * without w_given). */
+/* hotrg_plan_set_given_steps(plan, k0) (w_given plans): the following
+ * forwards use the stored isometries of steps 1..k0 and take those of later
+ * steps from the Gram matrix as HOTRG does (stored, so that a later call with
+ * a larger k0 uses them as parameters); 0 <= k0 <= n_steps, default n_steps.
+ * A forward needs defined isometries for steps 1..min(k0, steps run): loaded
+ * with hotrg_set_isometries or formed by an earlier forward.  This grows a
+ * network one layer at a time (scheme (b) cooling with differentiable-TRG
+ * optimisation of the newest layers). */
+hotrg_status hotrg_plan_set_given_steps(hotrg_plan plan, int k0);
 hotrg_status hotrg_isometries(hotrg_plan plan, double* w);
 hotrg_status hotrg_set_isometries(hotrg_plan plan, const double* w);
 hotrg_status hotrg_isometry_adjoints(hotrg_plan plan, double* wbar);
 hotrg_status hotrg_mera_update(hotrg_plan plan, int step);
+
+/* Quasi-Newton optimisation of one layer's isometry (SM Sec. D): w_k = exp(B)
+ * truncated to D' columns, B antisymmetric N x N (N = X_k^2), updated by
+ * L-BFGS to maximise ln Z / N with every other isometry fixed.  The run starts
+ * at the layer's current isometry: w_k(B) = Q exp(B) E with Q the complete
+ * Householder QR factor of w_k (columns sign-fixed so that Q E = w_k), E the
+ * first D' columns of the identity, B = 0 (the paper's exp(B) is Q = I).  The
+ * gradient comes from the plan's fixed-w backward (main-text Eq. (1)) through
+ * the adjoint Frechet derivative of the matrix exponential (the upper-right
+ * block of exp([[B^T, C], [0, B^T]]), C = Q^T wbar E^T); every matrix
+ * exponential is scaling and squaring of a degree-16 Taylor polynomial on the
+ * FP64 GEMM.  L-BFGS: two-loop recursion with `history` pairs and
+ * H_0 = (s^T y / y^T y) I, the first step along the gradient scaled to length
+ * step0 (radians of rotation), backtracking from the full step until the
+ * Armijo condition with constant c1 holds (at most max_backtracks halvings;
+ * a failed search ends the run), pairs with s^T y <= 0 not stored.  Cost
+ * O(N^3) = O(D^6) per evaluation (the paper's figure for this optimiser).
+ *
+ * hotrg_lbfgs_create: for a w_given plan (want_grad = fixed_w_grad = 1) that
+ *   has run a forward (its site tensor is reused); allocates the optimiser's
+ *   device memory (about (2 history + 20) N^2 doubles for the largest N).
+ * hotrg_lbfgs_layer: n_iter iterations on layer `step` (1 <= step <= the
+ *   steps the plan runs, with that step's isometry given); f_hist (host,
+ *   n_iter + 1 doubles, may be NULL) receives ln Z / N at the start and after
+ *   each accepted iteration, n_accepted / n_evals (may be NULL) the accepted
+ *   iterations and forward evaluations.  The plan keeps the last accepted
+ *   isometry.  Synchronises the plan's stream.
+ * hotrg_lbfgs_destroy: frees it (before its plan). */
+typedef struct hotrg_lbfgs_s* hotrg_lbfgs;
+hotrg_status hotrg_lbfgs_create(hotrg_plan plan, int history, hotrg_lbfgs* out);
+hotrg_status hotrg_lbfgs_layer(hotrg_lbfgs opt, int step, int n_iter, double step0, double c1,
+                               int max_backtracks, double* f_hist, int* n_accepted,
+                               int* n_evals);
+void hotrg_lbfgs_destroy(hotrg_lbfgs opt);
 
 /* sizeof(hotrg_config) as compiled into the library, so that a binding can
  * check that its copy of the struct matches. */
@@ -201,6 +266,22 @@ hotrg_status hotrg_forward_tensor(hotrg_plan plan, const double* T0_host,
  * beta*J >= 0 and d0 == 2.  Outputs as hotrg_forward_tensor. */
 hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double h,
                                  double* lnz_per_site, double* log_norms, int* trace_sign);
+
+/* Forward for the quantum XY chain H = J sum_i (S^x_i S^x_{i+1} + S^y_i S^y_{i+1})
+ * (main text, "Infinite quantum XY chain"; needs scheme = 1 and d0 == 4).  T0 is
+ * built on the device: the second-order Trotter MPO of rho(tau) (SM Sec. F),
+ * rho(tau) = e^{-tau/2 H_o} e^{-tau H_e} e^{-tau/2 H_o}, one tensor per
+ * two-site cell (u, d = the cell's two spins, 4 states; l, r = the operator-SVD
+ * index of the bond between cells, 4 values).  After n steps the output is
+ * lnz (see scheme) at beta = 2^(n+1) tau; ln Z per site = 2^n lnz, the free
+ * energy per site f = -2^n lnz / beta.  tau > 0.  Outputs (host, may be NULL)
+ * as hotrg_forward_tensor. */
+hotrg_status hotrg_forward_xy(hotrg_plan plan, double tau, double J, double* lnz_per_copy,
+                              double* log_norms);
+
+/* Scheme 1: lnz of every depth k = 1..n of the last forward (host array of
+ * the steps run); entries before the last are NaN unless chain_steps = 1. */
+hotrg_status hotrg_chain_lnz_steps(hotrg_plan plan, double* lnz_steps);
 
 /* Device-resident forward: T0_dev is a device pointer (d0^4 float64); results
  * are written to the device buffer out_dev = [lnz_per_site, trace_sign,

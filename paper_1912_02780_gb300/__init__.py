@@ -31,7 +31,9 @@ EXPORTS = (
     "hotrg_isometries", "hotrg_set_isometries", "hotrg_isometry_adjoints", "hotrg_mera_update", "hotrg_plan_create",
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
-    "hotrg_plan_set_steps", "hotrg_plan_set_stream",
+    "hotrg_plan_set_steps", "hotrg_plan_set_stream", "hotrg_plan_set_given_steps",
+    "hotrg_forward_xy", "hotrg_chain_lnz_steps",
+    "hotrg_lbfgs_create", "hotrg_lbfgs_layer", "hotrg_lbfgs_destroy",
     "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
     "hotrg_profile_enable", "hotrg_profile_read", "hotrg_kernel_launches",
@@ -56,7 +58,8 @@ class hotrg_config(ctypes.Structure):
                 ("epilogue_split", ctypes.c_int), ("split_chunk_elems", ctypes.c_longlong),
                 ("w_given", ctypes.c_int), ("eigh_residual_tol", ctypes.c_double),
                 ("stage2_n_group", ctypes.c_int), ("stage2_pair", ctypes.c_int),
-                ("gemm_sm_reserve", ctypes.c_int), ("eigh_warm_start", ctypes.c_int)]
+                ("gemm_sm_reserve", ctypes.c_int), ("eigh_warm_start", ctypes.c_int),
+                ("scheme", ctypes.c_int), ("chain_steps", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -143,12 +146,20 @@ def lib() -> ctypes.CDLL:
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
                         "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy",
-                        "hotrg_config_sizeof"):
+                        "hotrg_config_sizeof", "hotrg_lbfgs_destroy"):
             getattr(L, name).restype = ctypes.c_int
     L.hotrg_isometries.argtypes = [vp, _dp]
     L.hotrg_set_isometries.argtypes = [vp, _dp]
     L.hotrg_isometry_adjoints.argtypes = [vp, _dp]
     L.hotrg_mera_update.argtypes = [vp, ctypes.c_int]
+    L.hotrg_plan_set_given_steps.argtypes = [vp, ctypes.c_int]
+    L.hotrg_forward_xy.argtypes = [vp, ctypes.c_double, ctypes.c_double, _dp, _dp]
+    L.hotrg_chain_lnz_steps.argtypes = [vp, _dp]
+    L.hotrg_lbfgs_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
+    L.hotrg_lbfgs_layer.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
+                                    ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]
+    L.hotrg_lbfgs_destroy.argtypes = [vp]
+    L.hotrg_lbfgs_destroy.restype = None
     L.hotrg_config_sizeof.argtypes = []
     L.hotrg_config_sizeof.restype = ctypes.c_size_t
     if L.hotrg_config_sizeof() != ctypes.sizeof(hotrg_config):
@@ -170,7 +181,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 epilogue_split: bool = True, split_chunk_elems: int = 0,
                 w_given: bool = False, eigh_residual_tol: float = 0.0,
                 stage2_n_group: int = 0, stage2_pair: int = 0,
-                gemm_sm_reserve: int = 0, eigh_warm_start: int = 0) -> hotrg_config:
+                gemm_sm_reserve: int = 0, eigh_warm_start: int = 0, scheme: int = 0,
+                chain_steps: bool = False) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -191,6 +203,8 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.stage2_pair = int(stage2_pair)
     c.gemm_sm_reserve = int(gemm_sm_reserve)
     c.eigh_warm_start = int(eigh_warm_start)
+    c.scheme = int(scheme)
+    c.chain_steps = int(bool(chain_steps))
     return c
 
 
@@ -219,12 +233,13 @@ class Plan:
                  epilogue_split: bool = True, split_chunk_elems: int = 0,
                  w_given: bool = False, eigh_residual_tol: float = 0.0,
                  stage2_n_group: int = 0, stage2_pair: int = 0, gemm_sm_reserve: int = 0,
-                 eigh_warm_start: int = 0):
+                 eigh_warm_start: int = 0, scheme: int = 0, chain_steps: bool = False):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
                                epilogue_split, split_chunk_elems, w_given, eigh_residual_tol,
-                               stage2_n_group, stage2_pair, gemm_sm_reserve, eigh_warm_start)
+                               stage2_n_group, stage2_pair, gemm_sm_reserve, eigh_warm_start,
+                               scheme, chain_steps)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         self.n_run = n_steps
         h = ctypes.c_void_p(0)
@@ -262,6 +277,27 @@ class Plan:
         self._check(lib().hotrg_forward_ising(self._h, beta, J, h, ctypes.byref(lnz), _p(ln),
                                               ctypes.byref(sign)), "forward_ising")
         return lnz.value, ln, sign.value
+
+    def forward_xy(self, tau: float, J: float = 1.0):
+        """Scheme-1 forward of the quantum XY chain's Trotter MPO rho(tau):
+        (lnz per copy of T0 at beta = 2^(n+1) tau, log-norms)."""
+        lnz = ctypes.c_double(0)
+        ln = np.zeros(self.n_run)
+        self._check(lib().hotrg_forward_xy(self._h, tau, J, ctypes.byref(lnz), _p(ln)),
+                    "forward_xy")
+        return lnz.value, ln
+
+    def chain_lnz_steps(self):
+        """Scheme 1: lnz of every depth of the last forward (NaN before the
+        last unless the plan has chain_steps)."""
+        out = np.zeros(self.n_run)
+        self._check(lib().hotrg_chain_lnz_steps(self._h, _p(out)), "chain_lnz_steps")
+        return out
+
+    def set_given_steps(self, k0: int):
+        """w_given plans: steps 1..k0 use the stored isometries, later ones
+        form theirs from the Gram matrix."""
+        self._check(lib().hotrg_plan_set_given_steps(self._h, int(k0)), "set_given_steps")
 
     def forward_device(self, T0_ptr: int, out_ptr: int):
         self._check(lib().hotrg_forward_device(self._h, ctypes.c_void_p(T0_ptr),
@@ -368,6 +404,42 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class LBFGS:
+    """Quasi-Newton optimiser of one layer's isometry at a time in the
+    exponential parametrisation (see include/hotrg.h: hotrg_lbfgs_*), bound to
+    a w_given plan that has run a forward."""
+
+    def __init__(self, plan: "Plan", history: int = 10):
+        self.plan = plan
+        h = ctypes.c_void_p(0)
+        plan._check(lib().hotrg_lbfgs_create(plan._h, int(history), ctypes.byref(h)),
+                    "lbfgs_create")
+        self._h = h
+
+    def layer(self, step: int, n_iter: int, step0: float = 0.1, c1: float = 1e-4,
+              max_backtracks: int = 30):
+        """n_iter iterations on layer `step`: (ln Z/N at the start and after each
+        accepted iteration, forward evaluations)."""
+        f = np.zeros(n_iter + 1)
+        acc, ev = ctypes.c_int(0), ctypes.c_int(0)
+        self.plan._check(lib().hotrg_lbfgs_layer(self._h, int(step), int(n_iter), float(step0),
+                                                 float(c1), int(max_backtracks), _p(f),
+                                                 ctypes.byref(acc), ctypes.byref(ev)),
+                         "lbfgs_layer")
+        return f[:acc.value + 1], ev.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().hotrg_lbfgs_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
 
     def __enter__(self):
         return self

@@ -33,6 +33,7 @@
 #include "gemm_f64.h"
 #include "gemm_tc.h"
 #include "kernels.h"
+#include "plan_access.h"
 
 using namespace hotrg;
 
@@ -114,8 +115,12 @@ bool build_layout(const hotrg_config& c, Layout& L) {
       if (Xp * X * X > L.splitW1) L.splitW1 = Xp * X * X;
       if (Xp * X * X > L.splitW3) L.splitW3 = Xp * X * X;
     }
-    Y = Xp;           // T' is (Xp, Xp, Y, Y), stored re-oriented as (Y, Y, Xp, Xp)
-    X = s.Y;
+    if (c.scheme == 1) {
+      X = Xp;         // scheme (b): T' is stored (Xp, Xp, Y, Y), the vertical legs keep Y
+    } else {
+      Y = Xp;         // T' is (Xp, Xp, Y, Y), stored re-oriented as (Y, Y, Xp, Xp)
+      X = s.Y;
+    }
   }
   L.totalT += (long long)c.d0 * c.d0 * c.d0 * c.d0;
   L.chunkS = round_up(L.chunkS, 64);
@@ -183,6 +188,14 @@ struct hotrg_plan_s {
   double* svd_work = nullptr;
   double* svd_rwork = nullptr;
   int svd_lwork = 0;
+  // w_given plans: steps 1..given_steps use the stored isometries, later steps
+  // take theirs from the Gram matrix (scheme (b) cooling, one new layer at a time)
+  int given_steps = 0;
+  int w_valid = 0;    // leading steps whose stored isometries are defined
+  // scheme (b): dominant eigenvectors of the exact-product transfer operator
+  // (right one of the last forward, left one of the backward), power-iteration
+  // buffers, and out_k of every step
+  double *chR = nullptr, *chW = nullptr, *chV = nullptr, *chZ = nullptr, *lnz_steps = nullptr;
   std::string last_error;
   // optional per-stage CUDA-event timing
   bool prof = false;
@@ -280,6 +293,9 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->stage2_n_group < 0) return HOTRG_EINVAL;
   if (c->gemm_sm_reserve < 0 || c->gemm_sm_reserve > 64) return HOTRG_EINVAL;
   if (c->eigh_warm_start < 0 || c->eigh_warm_start > 16) return HOTRG_EINVAL;
+  if (c->scheme < 0 || c->scheme > 1 || c->chain_steps < 0 || c->chain_steps > 1)
+    return HOTRG_EINVAL;
+  if (c->scheme == 1 && c->d_cut > 4096) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -538,7 +554,8 @@ int subspace_k(const hotrg_config& c, const StepGeom& s) {
 }
 
 bool subspace_applies(const hotrg_config& c, const StepGeom& s) {
-  return c.eigh_mode == 1 && !c.want_grad && (long long)subspace_k(c, s) < s.N;
+  return c.eigh_mode == 1 && (!c.want_grad || c.fixed_w_grad) &&
+         (long long)subspace_k(c, s) < s.N;
 }
 
 bool use_subspace(const hotrg_plan p, const StepGeom& s) { return subspace_applies(p->cfg, s); }
@@ -703,6 +720,138 @@ hotrg_status guard_fired(hotrg_plan p, bool* fired) {
   return HOTRG_OK;
 }
 
+// ---- scheme (b): the exact final product ---------------------------------
+//
+// Main text Fig. 1b leaves a one-dimensional structure that is contracted
+// exactly.  For the depth-k chain T~_k[x][x'][y][j] (X x X x d x d) the free
+// energy is evaluated as Tr[rho rho] of two copies of the chain, whose cell
+// transfer operator acts on X x X matrices V as
+//     (A V)[x1][x2] = sum_{y, j} sum_{x1', x2'} T[x1][x1'][y][j] V[x1'][x2'] T[x2][x2'][j][y],
+// i.e. A V = sum_{y,j} T_yj V T_jy^T; the infinite chain contributes
+// ln lambda_max(A) per cell, so out_k = sum_j ln c_j / 2^j + ln lambda_max / 2^(k+1).
+// lambda_max and its eigenvectors come from power iteration in FP64 (two GEMMs
+// per product, through the same mixed-radix index maps as the contractions).
+
+constexpr int kChainMaxIters = 20000;   // power iterations before HOTRG_ENOTCONV
+constexpr int kChainCheck = 8;          // iterations between convergence reads
+constexpr double kChainTol = 1e-13;     // ||V_{i+1} - V_i||_F of unit vectors
+
+// out = A in (left = false) or A^T in (left = true), in/out X x X row-major.
+hotrg_status chain_apply(hotrg_plan p, const double* T, int X, int d, bool left, const double* in,
+                         double* out) {
+  cudaStream_t st = p->stream;
+  const long long d2 = (long long)d * d, Xd2 = X * d2, dX = (long long)d * X;
+  if (!left) {
+    // Z[(x1 y j)][x2'] = sum_{x1'} T[x1][x1'][y][j] V[x1'][x2']
+    CK(gemm_f64(g64(p, T, map3(d, d, 1, d, Xd2), map_lin(d2), in, map_lin(1), map_lin(X), p->chZ,
+                    map_lin(X), map_lin(1), X * (int)d2, X, X, 1.0, 0.0),
+                st, p->sms));
+    // out[x1][x2] = sum_{x2' j y} Z[(x1 y j)][x2'] T[x2][x2'][j][y]
+    CK(gemm_f64(g64(p, p->chZ, map_lin(d2 * X), map3(X, d, 1, X, dX), T, map_lin(Xd2),
+                    map3(X, d, d2, d, 1), out, map_lin(X), map_lin(1), X, X, X * (int)d2, 1.0,
+                    0.0),
+                st, p->sms));
+  } else {
+    // Z[(x1' y j)][x2] = sum_{x1} T[x1][x1'][y][j] W[x1][x2]
+    CK(gemm_f64(g64(p, T, map3(d, d, 1, d, d2), map_lin(Xd2), in, map_lin(1), map_lin(X), p->chZ,
+                    map_lin(X), map_lin(1), X * (int)d2, X, X, 1.0, 0.0),
+                st, p->sms));
+    // out[x1'][x2'] = sum_{x2 j y} Z[(x1' y j)][x2] T[x2][x2'][j][y]
+    CK(gemm_f64(g64(p, p->chZ, map_lin(d2 * X), map3(X, d, 1, X, dX), T, map_lin(d2),
+                    map3(X, d, Xd2, d, 1), out, map_lin(X), map_lin(1), X, X, X * (int)d2, 1.0,
+                    0.0),
+                st, p->sms));
+  }
+  return HOTRG_OK;
+}
+
+// Dominant eigenvector (unit Frobenius norm) of A (or A^T) into V, ln lambda_max
+// into p->scal[4].  Starts from the identity; fails with HOTRG_ENOTCONV when
+// the iteration does not settle (a dominant eigenvalue that is not real,
+// positive and simple).
+hotrg_status chain_power(hotrg_plan p, const double* T, int X, int d, bool left, double* V) {
+  cudaStream_t st = p->stream;
+  const long long n = (long long)X * X;
+  CK(eye_unit(V, X, st, p->sms));
+  double* cur = V;
+  double* nxt = p->chV;
+  bool done = false;
+  for (int it = 1; it <= kChainMaxIters && !done; ++it) {
+    hotrg_status r = chain_apply(p, T, X, d, left, cur, nxt);
+    if (r != HOTRG_OK) return r;
+    CK(frob_normalize(nxt, n, p->partial, kMaxPartial, p->scal + 4, p->scal + 5, p->err, st,
+                      p->sms));
+    CK(diff_norm(nxt, cur, n, p->scal + 6, st));
+    std::swap(cur, nxt);
+    if (it % kChainCheck == 0) {
+      double diff = 0;
+      CK(cudaMemcpyAsync(&diff, p->scal + 6, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (!(diff == diff)) return fail(p, HOTRG_ENONFINITE, "chain power iteration: not finite");
+      done = diff < kChainTol;
+    }
+  }
+  if (!done)
+    return fail(p, HOTRG_ENOTCONV, "chain power iteration: no simple positive dominant eigenvalue");
+  if (cur != V) CK(cudaMemcpyAsync(V, cur, sizeof(double) * n, cudaMemcpyDeviceToDevice, st));
+  return HOTRG_OK;
+}
+
+// out_k of the depth-k chain (T~_k in p->T[k]): the right eigenvector stays in
+// p->chR for the backward; out_k goes to p->out (k = the run's last step) and
+// to p->lnz_steps[k - 1].
+hotrg_status chain_value(hotrg_plan p, int k) {
+  const StepGeom& g = p->L.g[k - 1];
+  hotrg_status r = chain_power(p, p->T[k], g.Xp, g.Y, false, p->chR);
+  if (r != HOTRG_OK) return r;
+  CK(chain_lnz(p->log_norms, k, p->scal + 4, k == p->n_run ? p->out : nullptr,
+               p->lnz_steps + (k - 1), p->stream));
+  return HOTRG_OK;
+}
+
+// E_n = 2^n d out_n / d T~_n = (1/2) d ln lambda / d T~_n
+//     = [L T_vu R^T + L^T T_vu R][a][b] / (2 lambda <L, R>)   at [a][b][u][v],
+// with R, L the right and left dominant eigenvectors (X x X) of A.
+hotrg_status chain_seed(hotrg_plan p) {
+  const int n = p->n_run;
+  const StepGeom& g = p->L.g[n - 1];
+  const int X = g.Xp, d = g.Y;
+  const double* T = p->T[n];
+  cudaStream_t st = p->stream;
+  hotrg_status r = chain_power(p, T, X, d, true, p->chW);
+  if (r != HOTRG_OK) return r;
+  // the right eigenvector of the forward (the same tensor) is in p->chR
+  const long long d2 = (long long)d * d, Xd2 = X * d2, dX = (long long)d * X;
+  CK(dot_small(p->chW, p->chR, X * X, p->scal + 7, st));
+  double h[2] = {0, 0};
+  CK(cudaMemcpyAsync(&h[0], p->scal + 4, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaMemcpyAsync(&h[1], p->scal + 7, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  const double lam = std::exp(h[0]), lr = h[1];
+  if (!(lr != 0.0) || !std::isfinite(lam * lr))
+    return fail(p, HOTRG_ENONFINITE, "chain seed: eigenvectors orthogonal or not finite");
+  const double coef = 0.5 / (lam * lr);
+  // term 1: Y[(x2 u v)][b] = sum_{x2'} T[x2][x2'][v][u] R[b][x2'];
+  //         E[a][(b u v)]  = coef sum_{x2} L[a][x2] Y[(x2 u v)][b]
+  CK(gemm_f64(g64(p, T, map3(d, d, d, 1, Xd2), map_lin(d2), p->chR, map_lin(X), map_lin(1),
+                  p->chZ, map_lin(X), map_lin(1), X * (int)d2, X, X, 1.0, 0.0),
+              st, p->sms));
+  CK(gemm_f64(g64(p, p->chW, map_lin(X), map_lin(1), p->chZ, map3(d, d, X, dX, 1),
+                  map_lin(d2 * X), p->Ecur, map_lin(Xd2), map3(d, d, 1, d, d2), X, X * (int)d2, X,
+                  coef, 0.0),
+              st, p->sms));
+  // term 2: Y[(x1 u v)][b] = sum_{x1'} T[x1][x1'][v][u] R[x1'][b];
+  //         E[a][(b u v)] += coef sum_{x1} L[x1][a] Y[(x1 u v)][b]
+  CK(gemm_f64(g64(p, T, map3(d, d, d, 1, Xd2), map_lin(d2), p->chR, map_lin(1), map_lin(X),
+                  p->chZ, map_lin(X), map_lin(1), X * (int)d2, X, X, 1.0, 0.0),
+              st, p->sms));
+  CK(gemm_f64(g64(p, p->chW, map_lin(1), map_lin(X), p->chZ, map3(d, d, X, dX, 1),
+                  map_lin(d2 * X), p->Ecur, map_lin(Xd2), map3(d, d, 1, d, d2), X, X * (int)d2, X,
+                  coef, 1.0),
+              st, p->sms));
+  return HOTRG_OK;
+}
+
 // Extra power iterations the guard may add to a step before it hands the
 // step to the exact partial eigensolver (one iteration costs ~10 ms at
 // D = 64, the exact solver ~350 ms).
@@ -717,7 +866,7 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   double* lk = p->lam[k - 1];
   const int N = (int)s.N;
   hotrg_status r;
-  if (p->cfg.w_given) {
+  if (p->cfg.w_given && k <= p->given_steps) {
     // the isometries are parameters (differentiable-TRG sweeps): no Gram, no
     // eigensolve; truncation diagnostics are not defined
     CK(set_value(p->dtrunc + (k - 1), std::nan(""), nullptr, 0, st));
@@ -743,7 +892,10 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     CK(eigh_info_check(p->info, p->err, st));
     if (g_inj_what.load() == kInjEigh && g_inj_arg.load() == k)
       CK(set_value(nullptr, 0.0, p->err, kErrEigh, st));
-    CK(eig_desc(evec, p->wasc, N, ncols, p->cfg.want_grad ? N : s.Xp, Ek, lk, st));
+    // all N pairs where the backward's eigensolve adjoint needs the discarded
+    // ones and the solver returned them; the D' kept ones otherwise
+    CK(eig_desc(evec, p->wasc, N, ncols, (p->cfg.want_grad && ncols >= N) ? N : s.Xp, Ek, lk,
+                st));
     CK(eig_diag(lk, ncols, N, s.Xp, p->scal + 3, p->dtrunc + (k - 1), p->dgap + (k - 1), st));
     return HOTRG_OK;
   };
@@ -808,24 +960,36 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   const long long n_out = (long long)s.Y * s.Y * s.Xp * s.Xp;
   if (g_inj_what.load() == kInjNaN && g_inj_arg.load() == k)
     CK(set_value(Tout, std::nan(""), nullptr, 0, st));
+  {
   Stage sc(p, kStNorm);
   CK(frob_normalize(Tout, n_out, p->partial, kMaxPartial, p->log_norms + (k - 1), p->scal, p->err,
                     st, p->sms));
+  }
+  if (p->cfg.scheme == 1) {
+    // scheme (b): no re-orientation, the next step merges vertically again
+    CK(swap_pairs(Tout, p->Abuf, s.Y, s.Xp, st, p->sms));
+    CK(cudaMemcpyAsync(Tout, p->Abuf, sizeof(double) * n_out, cudaMemcpyDeviceToDevice, st));
+    if (p->cfg.chain_steps && k < p->n_run) return chain_value(p, k);
+  }
   return HOTRG_OK;
 }
 
 hotrg_status run_forward(hotrg_plan p) {
   cudaStream_t st = p->stream;
-  if (p->cfg.w_given && !p->w_loaded)
+  if (p->cfg.w_given && std::min(p->given_steps, p->n_run) > p->w_valid)
     return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
   p->have_bwd = false;
   p->guard_iters.assign(p->cfg.n_steps, 0);
   p->wkeep_n[0] = p->wkeep_n[1] = 0;   // no warm start across forwards
   p->exact_step.assign(p->cfg.n_steps, 0);
+  if (p->lnz_steps) CK(cudaMemsetAsync(p->lnz_steps, 0xff, sizeof(double) * p->cfg.n_steps, st));
   for (int k = 1; k <= p->n_run; ++k) {
     hotrg_status r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
   }
+  // steps past given_steps of a w_given plan have just formed their isometries
+  if (p->cfg.w_given && p->n_run > p->w_valid) p->w_valid = p->n_run;
+  if (p->cfg.scheme == 1) return chain_value(p, p->n_run);
   const StepGeom& last = p->L.g[p->n_run - 1];
   CK(trace_lnz(p->T[p->n_run], last.Y, last.Xp, p->log_norms, p->n_run, p->out,
                p->scal + 1, p->err, st));
@@ -889,6 +1053,14 @@ hotrg_status step_backward(hotrg_plan p, int k) {
   const double* T = p->T[k - 1];
   const double* Ek = E_of(p, k);
   const double* lk = p->lam[k - 1];
+  if (p->cfg.scheme == 1) {
+    // scheme (b) keeps T~_k (and so E_k) as [a][b][y][y']: bring E_k into the
+    // [y][y'][a][b] layout of the step's output index maps
+    CK(swap_pairs(p->Ecur, p->Enext, Xp, Y, st, p->sms));
+    double* t = p->Ecur;
+    p->Ecur = p->Enext;
+    p->Enext = t;
+  }
   double* Eb = p->Ecur;                    // 2^k dL/dT~_k, stored layout [y][y'][a][b]
   CK(scale_exp_neg(Eb, Y2 * Xp2, p->log_norms + (k - 1), st, p->sms));   // -> dL/dT' (x 2^k)
   CK(cudaMemsetAsync(p->Tbar, 0, sizeof(double) * X2 * Y2, st));
@@ -988,7 +1160,12 @@ hotrg_status step_backward(hotrg_plan p, int k) {
 
 hotrg_status run_backward(hotrg_plan p) {
   const StepGeom& last = p->L.g[p->n_run - 1];
-  CK(seed_trace_adjoint(p->Ecur, last.Y, last.Xp, p->scal + 1, p->stream, p->sms));
+  if (p->cfg.scheme == 1) {
+    hotrg_status r = chain_seed(p);
+    if (r != HOTRG_OK) return r;
+  } else {
+    CK(seed_trace_adjoint(p->Ecur, last.Y, last.Xp, p->scal + 1, p->stream, p->sms));
+  }
   for (int k = p->n_run; k >= 1; --k) {
     hotrg_status r = step_backward(p, k);
     if (r != HOTRG_OK) return r;
@@ -1018,6 +1195,21 @@ hotrg_status finish_sync(hotrg_plan p) {
 
 namespace hotrg {
 void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+cudaStream_t plan_stream(hotrg_plan p) { return p->stream; }
+int plan_sms(hotrg_plan p) { return p->sms; }
+int* plan_err(hotrg_plan p) { return p->err; }
+double* plan_isometry(hotrg_plan p, int k) { return p->E[k - 1]; }
+const double* plan_wbar(hotrg_plan p, int k) {
+  return p->wbar_all ? p->wbar_all + p->w_off[k - 1] : nullptr;
+}
+const double* plan_T0(hotrg_plan p) { return p->T[0]; }
+const double* plan_lnz(hotrg_plan p) { return p->out; }
+bool plan_has_forward(hotrg_plan p) { return p->have_fwd; }
+bool plan_w_given(hotrg_plan p) { return p->cfg.w_given != 0; }
+int plan_given_steps(hotrg_plan p) { return p->given_steps; }
+int plan_steps_run(hotrg_plan p) { return p->n_run; }
+hotrg_status plan_fail(hotrg_plan p, hotrg_status s, const char* msg) { return fail(p, s, msg); }
 }  // namespace hotrg
 
 extern "C" {
@@ -1116,6 +1308,8 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->stage2_pair = 0;
   c->gemm_sm_reserve = 0;
   c->eigh_warm_start = 0;
+  c->scheme = 0;
+  c->chain_steps = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -1157,6 +1351,12 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
       b.add(kmax * kmax, 8);
     }
   }
+  if (c->scheme == 1) {
+    const long long Xm = L.maxXp > c->d0 ? L.maxXp : c->d0;
+    b.add(Xm * Xm, 8 * 3);                                // chain eigenvectors
+    b.add(Xm * Xm * (long long)c->d0 * c->d0, 8);         // chain GEMM buffer
+    b.add(c->n_steps, 8);
+  }
   b.total += (size_t)64 << 20;  // solver workspace and small buffers (estimate)
   *bytes = b.total;
   return HOTRG_OK;
@@ -1169,6 +1369,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
   hotrg_plan p = new hotrg_plan_s();
   p->cfg = *cfg;
   p->n_run = cfg->n_steps;
+  p->given_steps = cfg->n_steps;
   if (!build_layout(*cfg, p->L)) {
     delete p;
     return HOTRG_EINVAL;
@@ -1301,7 +1502,7 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
     ALC(p->wkeep[0], L.maxN * L.maxXp);
     ALC(p->wkeep[1], L.maxN * L.maxXp);
   }
-  if (cfg->eigh_mode == 1 && !cfg->want_grad) {
+  if (cfg->eigh_mode == 1 && (!cfg->want_grad || cfg->fixed_w_grad)) {
     int kmax = 0;
     long long nmax = 0;
     for (const StepGeom& g : L.g)
@@ -1330,6 +1531,15 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       p->lswork = ls;
       ALC(p->swork, (long long)ls);
     }
+  }
+  if (cfg->scheme == 1) {
+    const long long Xm = L.maxXp > cfg->d0 ? L.maxXp : cfg->d0;
+    const long long d2 = (long long)cfg->d0 * cfg->d0;
+    ALC(p->chR, Xm * Xm);
+    ALC(p->chW, Xm * Xm);
+    ALC(p->chV, Xm * Xm);
+    ALC(p->chZ, Xm * Xm * d2);
+    ALC(p->lnz_steps, n);
   }
   if (cudaMallocHost(&p->guard_host, sizeof(int)) != cudaSuccess) {
     p->guard_host = nullptr;
@@ -1458,7 +1668,7 @@ hotrg_status hotrg_plan_set_stream(hotrg_plan p, void* cuda_stream) {
 
 hotrg_status hotrg_plan_set_steps(hotrg_plan p, int n_steps) {
   if (!p) return HOTRG_EINVAL;
-  if (n_steps < 1 || n_steps > p->cfg.n_steps || (p->cfg.w_given && n_steps != p->cfg.n_steps))
+  if (n_steps < 1 || n_steps > p->cfg.n_steps)
     return fail(p, HOTRG_EINVAL, "steps must be in [1, the plan's n_steps]");
   if (n_steps != p->n_run) p->have_fwd = p->have_bwd = false;
   p->n_run = n_steps;
@@ -1530,6 +1740,7 @@ hotrg_status hotrg_set_isometries(hotrg_plan p, const double* w) {
   hotrg_status r = finish_sync(p);
   if (r != HOTRG_OK) return r;
   p->w_loaded = true;
+  p->w_valid = p->cfg.n_steps;
   p->have_fwd = p->have_bwd = false;
   return HOTRG_OK;
 }
@@ -1543,8 +1754,38 @@ hotrg_status hotrg_isometry_adjoints(hotrg_plan p, double* wbar) {
   return finish_sync(p);
 }
 
+hotrg_status hotrg_plan_set_given_steps(hotrg_plan p, int k0) {
+  if (!p) return HOTRG_EINVAL;
+  if (!p->cfg.w_given) return fail(p, HOTRG_ESTATE, "plan created with w_given = 0");
+  if (k0 < 0 || k0 > p->cfg.n_steps) return fail(p, HOTRG_EINVAL, "k0 must be in [0, n_steps]");
+  if (k0 != p->given_steps) p->have_fwd = p->have_bwd = false;
+  p->given_steps = k0;
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_forward_xy(hotrg_plan p, double tau, double J, double* lnz, double* log_norms) {
+  if (!p) return HOTRG_EINVAL;
+  if (p->cfg.scheme != 1 || p->cfg.d0 != 4)
+    return fail(p, HOTRG_EINVAL, "the XY-chain MPO needs scheme = 1 and d0 == 4");
+  if (!std::isfinite(tau) || !std::isfinite(J) || tau <= 0)
+    return fail(p, HOTRG_EINVAL, "tau must be finite and positive, J finite");
+  CK(xy_mpo(tau, J, p->T[0], p->stream));
+  hotrg_status r = hotrg_forward_device(p, p->T[0], nullptr);
+  if (r != HOTRG_OK) return r;
+  return copy_out(p, lnz, log_norms, nullptr);
+}
+
+hotrg_status hotrg_chain_lnz_steps(hotrg_plan p, double* out) {
+  if (!p || !out) return HOTRG_EINVAL;
+  if (p->cfg.scheme != 1) return fail(p, HOTRG_ESTATE, "plan created with scheme = 0");
+  if (!p->have_fwd) return fail(p, HOTRG_ESTATE, "no forward yet");
+  CK(cudaMemcpyAsync(out, p->lnz_steps, sizeof(double) * p->n_run, cudaMemcpyDeviceToHost,
+                     p->stream));
+  return finish_sync(p);
+}
+
 hotrg_status hotrg_mera_update(hotrg_plan p, int k) {
-  if (!p || k < 1 || k > p->cfg.n_steps) return HOTRG_EINVAL;
+  if (!p || k < 1 || k > p->n_run) return HOTRG_EINVAL;
   if (!p->cfg.w_given) return fail(p, HOTRG_ESTATE, "plan created with w_given = 0");
   if (!p->have_bwd) return fail(p, HOTRG_ESTATE, "the MERA update needs a backward first");
   const StepGeom& g = p->L.g[k - 1];

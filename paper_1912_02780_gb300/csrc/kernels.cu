@@ -531,6 +531,114 @@ __global__ void dot16_kernel(const double* __restrict__ a, const double* __restr
   }
 }
 
+
+// out[c][d][a][b] = in[a][b][c][d], in of shape (P, P, Q, Q): the exchange of
+// the leg pairs (l, r) <-> (u, d).
+__global__ void swap_pairs_kernel(const double* __restrict__ in, double* __restrict__ out, int P,
+                                  int Q) {
+  const long long n = (long long)P * P * Q * Q, q2 = (long long)Q * Q;
+  for (long long i = gtid(); i < n; i += gstride()) {
+    const long long ab = i / q2, cd = i - ab * q2;
+    out[cd * P * P + ab] = in[i];
+  }
+}
+
+// Density-matrix MPO cell of the quantum XY chain, rho(tau) to second order in
+// tau: T0[l][r][(s1 s2)][(v1 v2)] = sum g_odd[(s1 s2),(t1 t2)] R_l[t1,t1']
+// L_r[t2,t2'] g_odd[(t1' t2'),(v1 v2)], with g_odd = exp(-tau/2 h) on the cell's
+// own bond and exp(-tau h) = sum_k L_k (x) R_k on the bond to the next cell.
+// h = J (SxSx + SySy) flips |01> <-> |10> with amplitude J/2 (state 0 = up), so
+// exp(-t h) is the identity on |00>, |11> and [[ch, -sh], [-sh, ch]] on
+// (|01>, |10>), ch = cosh(t J / 2), sh = sinh(t J / 2).  In Pauli form
+// exp(-t h) = (1+ch)/2 1(x)1 + (1-ch)/2 Z(x)Z - sh/2 X(x)X + sh/2 (iY)(x)(iY),
+// (iY = [[0, 1], [-1, 0]]), an operator SVD across the bond:
+// L_k = sqrt|c_k| P_k, R_k = sign(c_k) sqrt|c_k| P_k.
+__device__ double xy_gate(double t, double J, int s1, int s2, int t1, int t2) {
+  const int a = 2 * s1 + s2, b = 2 * t1 + t2;
+  if (a == 0 || a == 3) return a == b ? 1.0 : 0.0;
+  if (b == 0 || b == 3) return 0.0;
+  return a == b ? cosh(0.5 * t * J) : -sinh(0.5 * t * J);
+}
+
+__device__ double pauli(int k, int a, int b) {
+  switch (k) {
+    case 0: return a == b ? 1.0 : 0.0;                       // 1
+    case 1: return a == b ? (a == 0 ? 1.0 : -1.0) : 0.0;     // Z
+    case 2: return a != b ? 1.0 : 0.0;                       // X
+    default: return a == b ? 0.0 : (a == 0 ? 1.0 : -1.0);    // iY
+  }
+}
+
+__global__ void xy_mpo_kernel(double tau, double J, double* __restrict__ T0) {
+  const int idx = threadIdx.x;   // (l, r, s1, s2, v1, v2): 4 * 4 * 16 entries
+  if (idx >= 256) return;
+  const int l = idx >> 6, r = (idx >> 4) & 3, s1 = (idx >> 3) & 1, s2 = (idx >> 2) & 1,
+            v1 = (idx >> 1) & 1, v2 = idx & 1;
+  const double ch = cosh(0.5 * tau * J), sh = sinh(0.5 * tau * J);
+  const double c[4] = {0.5 * (1.0 + ch), 0.5 * (1.0 - ch), -0.5 * sh, 0.5 * sh};
+  const double sl = (c[l] < 0 ? -1.0 : 1.0) * sqrt(fabs(c[l]));   // R_l
+  const double sr = sqrt(fabs(c[r]));                             // L_r
+  double acc = 0.0;
+  for (int t1 = 0; t1 < 2; ++t1)
+    for (int t2 = 0; t2 < 2; ++t2) {
+      const double top = xy_gate(0.5 * tau, J, s1, s2, t1, t2);
+      if (top == 0.0) continue;
+      for (int u1 = 0; u1 < 2; ++u1)
+        for (int u2 = 0; u2 < 2; ++u2) {
+          const double mid = sl * pauli(l, t1, u1) * sr * pauli(r, t2, u2);
+          if (mid == 0.0) continue;
+          acc += top * mid * xy_gate(0.5 * tau, J, u1, u2, v1, v2);
+        }
+    }
+  T0[idx] = acc;
+}
+
+// *out = ||a - b||_F (one block; power-iteration convergence test).
+__global__ void diff_norm_kernel(const double* __restrict__ a, const double* __restrict__ b,
+                                 long long n, double* __restrict__ out) {
+  __shared__ double ws[32];
+  double s = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) {
+    const double d = a[i] - b[i];
+    s = fma(d, d, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += ws[w];
+    *out = sqrt(t);
+  }
+}
+
+// v = sum_k log_norms[k] / 2^(k+1) + lnlam / 2^(n+1); out (if given) =
+// [v, 1, log_norms...]; *step_out (if given) = v.
+__global__ void chain_lnz_kernel(const double* __restrict__ log_norms, int n,
+                                 const double* __restrict__ lnlam, double* __restrict__ out,
+                                 double* __restrict__ step_out) {
+  if (threadIdx.x != 0) return;
+  double acc = 0.0, scale = 1.0;
+  for (int k = 0; k < n; ++k) {
+    scale *= 0.5;
+    acc += log_norms[k] * scale;
+  }
+  const double v = acc + *lnlam * scale * 0.5;
+  if (out) {
+    out[0] = v;
+    out[1] = 1.0;
+    for (int k = 0; k < n; ++k) out[2 + k] = log_norms[k];
+  }
+  if (step_out) *step_out = v;
+}
+
+// Identity matrix (X x X) scaled to unit Frobenius norm.
+__global__ void eye_unit_kernel(double* __restrict__ V, int X) {
+  const long long n = (long long)X * X;
+  const double v = 1.0 / sqrt((double)X);
+  for (long long i = gtid(); i < n; i += gstride()) V[i] = (i / X == i % X) ? v : 0.0;
+}
+
 }  // namespace
 
 cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
@@ -711,6 +819,38 @@ cudaError_t set_value(double* x, double v, int* err, int bits, cudaStream_t st) 
 cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st) {
   count_launch();
   dot16_kernel<<<1, 32, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t swap_pairs(const double* in, double* out, int P, int Q, cudaStream_t st, int sms) {
+  count_launch();
+  swap_pairs_kernel<<<blocks_for((long long)P * P * Q * Q, sms), 256, 0, st>>>(in, out, P, Q);
+  return cudaGetLastError();
+}
+
+cudaError_t xy_mpo(double tau, double J, double* T0, cudaStream_t st) {
+  count_launch();
+  xy_mpo_kernel<<<1, 256, 0, st>>>(tau, J, T0);
+  return cudaGetLastError();
+}
+
+cudaError_t diff_norm(const double* a, const double* b, long long n, double* out,
+                      cudaStream_t st) {
+  count_launch();
+  diff_norm_kernel<<<1, 1024, 0, st>>>(a, b, n, out);
+  return cudaGetLastError();
+}
+
+cudaError_t chain_lnz(const double* log_norms, int n, const double* lnlam, double* out,
+                      double* step_out, cudaStream_t st) {
+  count_launch();
+  chain_lnz_kernel<<<1, 32, 0, st>>>(log_norms, n, lnlam, out, step_out);
+  return cudaGetLastError();
+}
+
+cudaError_t eye_unit(double* V, int X, cudaStream_t st, int sms) {
+  count_launch();
+  eye_unit_kernel<<<blocks_for((long long)X * X, sms), 256, 0, st>>>(V, X);
   return cudaGetLastError();
 }
 

@@ -48,5 +48,17 @@ cudaError_t fill_random(double* x, long long n, unsigned long long seed, cudaStr
 // *x = v (if x) and *err |= bits (if err): used by the fault-injection hooks.
 cudaError_t set_value(double* x, double v, int* err, int bits, cudaStream_t st);
 cudaError_t dot_small(const double* a, const double* b, int n, double* out, cudaStream_t st);
+// out[c][d][a][b] = in[a][b][c][d] for in of shape (P, P, Q, Q).
+cudaError_t swap_pairs(const double* in, double* out, int P, int Q, cudaStream_t st, int sms);
+// T0 (4 x 4 x 4 x 4) of the quantum XY chain's second-order Trotter MPO rho(tau).
+cudaError_t xy_mpo(double tau, double J, double* T0, cudaStream_t st);
+// *out = ||a - b||_F (n up to a few million).
+cudaError_t diff_norm(const double* a, const double* b, long long n, double* out, cudaStream_t st);
+// Scheme-(b) value of a depth-n chain, v = sum_k ln c_k / 2^k + lnlam / 2^(n+1):
+// out (if not NULL) = [v, 1, ln c_1 .. ln c_n]; *step_out (if not NULL) = v.
+cudaError_t chain_lnz(const double* log_norms, int n, const double* lnlam, double* out,
+                      double* step_out, cudaStream_t st);
+// V = identity / sqrt(X) (X x X).
+cudaError_t eye_unit(double* V, int X, cudaStream_t st, int sms);
 
 }  // namespace hotrg

@@ -97,3 +97,26 @@ def test_dtrg_improves_on_hotrg_near_criticality():
     for beta, e_h, e_d in rows:
         if abs(beta - synth.BETA_C) > 1e-3:
             assert e_d < e_h
+
+
+@pytest.mark.parametrize("layers", [None, [3]])
+def test_lbfgs_sweeps_against_oracle(layers):
+    """L-BFGS in the exponential parametrisation (SM Sec. D) on the GPU against
+    the oracle's iterates, layer by layer, on the Ising network at beta = 0.40."""
+    from oracle import ising, lbfgs as olb
+    from paper_1912_02780_gb300 import dtrg as gd
+    beta, D, n = 0.40, 6, 8
+    n_iter = 5 if layers is None else 30
+    T0 = ising.ising_T0(beta, 1.0, 0.0)
+    ref = olb.lbfgs_sweeps(T0, D, n, n_sweeps=1, n_iter=n_iter, layers=layers)
+    got = gd.lbfgs_sweeps(2, D, n, n_sweeps=1, n_iter=n_iter, beta=beta, layers=layers)
+    assert abs(got["lnz_hotrg"] - ref["lnz_hotrg"]) < 1e-13
+    for a, b in zip(got["layer_hist"], ref["layer_hist"]):
+        assert len(a) == len(b)
+        assert np.abs(np.asarray(a) - np.asarray(b)).max() < 1e-12
+    assert abs(got["lnz"][-1] - ref["lnz"][-1]) < 1e-12
+    assert got["lnz"][-1] > got["lnz_hotrg"]
+    for w in got["isometries"]:
+        X1, X2, Dp = w.shape
+        m = w.reshape(X1 * X2, Dp)
+        assert np.abs(m.T @ m - np.eye(Dp)).max() < 1e-12
