@@ -84,6 +84,7 @@ import math
 import numpy as np
 
 ETA_REL_DEFAULT = 1e-12
+W_RULE_TIE = 1e-12   # relative tie band of the w_rule = 1 comparison
 
 
 def orient(T: np.ndarray) -> np.ndarray:
@@ -138,13 +139,41 @@ def hotrg_step(T: np.ndarray, w: np.ndarray) -> np.ndarray:
     return out
 
 
+def swap_lr(T: np.ndarray) -> np.ndarray:
+    """T[l, r, u, d] -> T[r, l, u, d] (an involution)."""
+    return np.ascontiguousarray(T.transpose(1, 0, 2, 3))
+
+
+def choose_isometry(T: np.ndarray, d_cut: int, w_rule: int = 0):
+    """Eigenpairs of the Gram matrix that gives the isometry of this step and
+    the side it came from (0 = left, 1 = right).
+
+    w_rule 0: the left Gram matrix, always.  w_rule 1 (Xie2012's rule): the
+    HOSVD of the merged pair along its left bond (x1 x2) and along its right
+    bond (x1' x2'); the side whose discarded eigenvalues sum to less (the two
+    Gram matrices have the same trace) gives w, the left one on a tie.  A tie
+    is a difference of at most W_RULE_TIE times the trace: on a tensor whose
+    two sides have the same spectrum the sums differ by rounding only.  The
+    right Gram matrix is the left one of the tensor with l and r exchanged."""
+    X = T.shape[0]
+    lam, U = eigh_desc(gram(T))
+    Dp = min(X * X, d_cut)
+    if w_rule == 1 and Dp < X * X:
+        lamR, UR = eigh_desc(gram(swap_lr(T)))
+        eL, eR = float(np.sum(lam[Dp:])), float(np.sum(lamR[Dp:]))
+        if eL - eR > W_RULE_TIE * float(np.sum(lam)):
+            return lamR, UR, 1
+    return lam, U, 0
+
+
 def trace(T: np.ndarray) -> float:
     """Periodic self-contraction sum_{x, y} T[x, x, y, y] (main text: the
     single remaining tensor's self-contraction gives Z)."""
     return float(np.einsum("xxyy->", T))
 
 
-def hotrg_forward(T0, d_cut: int, n_steps: int, keep: bool = True, w_override=None):
+def hotrg_forward(T0, d_cut: int, n_steps: int, keep: bool = True, w_override=None,
+                  w_rule: int = 0):
     """HOTRG forward.  Returns a dict with
 
     lnz         ln Z / N (N = 2^n_steps sites)
@@ -158,7 +187,8 @@ def hotrg_forward(T0, d_cut: int, n_steps: int, keep: bool = True, w_override=No
     T_final     the last normalised tensor
 
     ``w_override(k, X, Dp, lam, U) -> w`` may replace the isometry of step k
-    (used only by invariance pins).
+    (used only by invariance pins).  ``w_rule``: which Gram matrix gives the
+    isometry (see ``choose_isometry``); the checkpoint records the side.
     """
     T = np.array(T0, dtype=np.float64)
     if T.ndim != 4 or T.shape[0] != T.shape[1] or T.shape[2] != T.shape[3]:
@@ -170,8 +200,7 @@ def hotrg_forward(T0, d_cut: int, n_steps: int, keep: bool = True, w_override=No
             T = orient(T)
         X = T.shape[0]
         N = X * X
-        G = gram(T)
-        lam, U = eigh_desc(G)
+        lam, U, side = choose_isometry(T, d_cut, w_rule)
         Dp = min(N, d_cut)
         if w_override is not None:
             w = w_override(k, X, Dp, lam, U)
@@ -185,7 +214,7 @@ def hotrg_forward(T0, d_cut: int, n_steps: int, keep: bool = True, w_override=No
         trunc.append(float(np.sum(lam[Dp:])) / total if total != 0 else 0.0)
         gaps.append(float((lam[Dp - 1] - lam[Dp]) / lam[0]) if Dp < N else math.inf)
         if keep:
-            ckpt.append(dict(T=T, w=w, lam=lam, U=U, c=c, Dp=Dp))
+            ckpt.append(dict(T=T, w=w, lam=lam, U=U, c=c, Dp=Dp, side=side))
         T = Tn / c
     tr = trace(T)
     lnz = S + math.log(abs(tr)) / 2.0 ** n_steps
@@ -277,7 +306,10 @@ def hotrg_backward(fwd, fixed_w: bool = False, eta_rel: float = ETA_REL_DEFAULT,
         if not fixed_w:
             Gbar = eigh_backward(ck["lam"], ck["U"], ck["Dp"], wbar, eta_rel)
             if np.any(Gbar):
-                Tbar = Tbar + gram_backward(T, Gbar)
+                if ck.get("side", 0) == 1:
+                    Tbar = Tbar + swap_lr(gram_backward(swap_lr(T), Gbar))
+                else:
+                    Tbar = Tbar + gram_backward(T, Gbar)
         E = 0.5 * (orient(Tbar) if k > 1 else Tbar)
     if return_wbar:
         return E, wbars

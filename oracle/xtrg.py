@@ -95,7 +95,7 @@ def dominant(M: np.ndarray):
 
 
 def xtrg_forward(T0, d_cut: int, n_steps: int, ws=None, keep: bool = True,
-                 evaluate: bool = True):
+                 evaluate: bool = True, w_rule: int = 0):
     """Vertical-only coarse-graining of the MPO cell tensor T0[l, r, u, d].
 
     ``ws``: isometries per step (w[x1, x2, a]); an entry None (or a list
@@ -114,8 +114,9 @@ def xtrg_forward(T0, d_cut: int, n_steps: int, ws=None, keep: bool = True,
         N = X * X
         w = ws[k - 1] if (ws is not None and k - 1 < len(ws)) else None
         lam = U = None
+        side = 0
         if w is None:
-            lam, U = hotrg.eigh_desc(hotrg.gram(T))
+            lam, U, side = hotrg.choose_isometry(T, d_cut, w_rule)
             Dp = min(N, d_cut)
             w = U[:, :Dp].reshape(X, X, Dp)
         w = np.asarray(w, dtype=np.float64)
@@ -126,7 +127,7 @@ def xtrg_forward(T0, d_cut: int, n_steps: int, ws=None, keep: bool = True,
         log_norms.append(math.log(c))
         S += math.log(c) / 2.0 ** k
         if keep:
-            ckpt.append(dict(T=T, w=w, lam=lam, U=U, c=c, Dp=w.shape[2]))
+            ckpt.append(dict(T=T, w=w, lam=lam, U=U, c=c, Dp=w.shape[2], side=side))
         T = Tn / c
         if evaluate:
             lnz_steps.append(S + math.log(dominant(square_transfer(T))[0]) / 2.0 ** (k + 1))
@@ -157,7 +158,10 @@ def xtrg_backward(fwd, fixed_w: bool = False, eta_rel: float = hotrg.ETA_REL_DEF
         if not fixed_w and ck["U"] is not None:
             Gbar = hotrg.eigh_backward(ck["lam"], ck["U"], ck["Dp"], wbar, eta_rel)
             if np.any(Gbar):
-                Tbar = Tbar + hotrg.gram_backward(T, Gbar)
+                if ck["side"] == 1:
+                    Tbar = Tbar + hotrg.swap_lr(hotrg.gram_backward(hotrg.swap_lr(T), Gbar))
+                else:
+                    Tbar = Tbar + hotrg.gram_backward(T, Gbar)
         E = 0.5 * Tbar
     if return_wbar:
         return E, wbars

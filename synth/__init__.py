@@ -16,6 +16,8 @@ input is synthetic):
   entries N(0, 1), made symmetric under the lattice reflections l<->r and
   u<->d by averaging the four reflected copies, then scaled so that
   max|T| = 1.
+* ``random_T0``: the same draw without the symmetrisation (a tensor whose
+  left and right environments differ).
 * ``serving_stream``: a seeded Poisson stream of Ising solve requests.
 """
 from __future__ import annotations
@@ -46,6 +48,14 @@ def random_symmetric_T0(seed: int, d0: int = 4) -> np.ndarray:
                 + t.transpose(1, 0, 3, 2))
     t = t / np.abs(t).max()
     return np.ascontiguousarray(t, dtype=np.float64)
+
+
+def random_T0(seed: int, d0: int = 4) -> np.ndarray:
+    """Random rank-4 tensor T[l, r, u, d] with N(0, 1) entries
+    (``default_rng(seed)``), divided by its largest magnitude."""
+    rng = np.random.default_rng(seed)
+    t = rng.standard_normal(d0 ** 4).reshape(d0, d0, d0, d0)
+    return np.ascontiguousarray(t / np.abs(t).max(), dtype=np.float64)
 
 
 def serving_stream(seed: int = 2024, n: int = 10000, rate: float = 200.0,

@@ -260,3 +260,51 @@ def test_w_gradient_matches_finite_differences():
                                             w_override=lambda k, X, Dp, lam, U: wk[k - 1])["lnz"])
         fd = (vals[0] - vals[1]) / (2 * e)
         assert abs(wbars[kk - 1][idx] - fd) < 1e-8 * max(1.0, abs(fd))
+
+
+# ---- w_rule = 1: the isometry from the side with the smaller truncation error
+
+def test_w_rule_1_equals_left_rule_on_reflection_symmetric_tensors():
+    import synth
+    for T0 in (ising.ising_T0(0.44, 1.0, 0.0), synth.random_symmetric_T0(0, 4)):
+        a = hotrg.hotrg_forward(T0, 6, 6)
+        b = hotrg.hotrg_forward(T0, 6, 6, w_rule=1)
+        assert a["lnz"] == b["lnz"]
+        assert all(ck["side"] == 0 for ck in b["ckpt"])
+
+
+def test_w_rule_1_takes_the_smaller_truncation_error_on_each_step():
+    import synth
+    T0 = synth.random_T0(3, 3)
+    fwd = hotrg.hotrg_forward(T0, 5, 6, w_rule=1)
+    sides = []
+    for ck in fwd["ckpt"]:
+        T, Dp = ck["T"], ck["Dp"]
+        lamL = hotrg.eigh_desc(hotrg.gram(T))[0]
+        lamR = hotrg.eigh_desc(hotrg.gram(hotrg.swap_lr(T)))[0]
+        assert abs(np.sum(lamL) - np.sum(lamR)) < 1e-12 * np.sum(lamL)   # same trace
+        eL, eR = np.sum(lamL[Dp:]), np.sum(lamR[Dp:])
+        want = 1 if eL - eR > hotrg.W_RULE_TIE * np.sum(lamL) else 0
+        assert ck["side"] == want
+        assert abs(np.sum(ck["lam"][Dp:]) - (eR if want else eL)) <= 1e-15 * np.sum(lamL)
+        sides.append(ck["side"])
+    assert 1 in sides and 0 in sides          # the rule actually switches on this input
+
+
+def test_w_rule_1_gradient_against_finite_differences_and_euler_identity():
+    import synth
+    T0 = synth.random_T0(3, 3)
+    D, n = 5, 4
+    fwd = hotrg.hotrg_forward(T0, D, n, w_rule=1)
+    g = hotrg.hotrg_backward(fwd)
+    f = lambda T: hotrg.hotrg_forward(T, D, n, keep=False, w_rule=1)["lnz"]
+    rng = np.random.default_rng(0)
+    for flat in rng.choice(T0.size, 10, replace=False):
+        idx = np.unravel_index(flat, T0.shape)
+        Tp, Tm = T0.copy(), T0.copy()
+        Tp[idx] += 1e-6
+        Tm[idx] -= 1e-6
+        fd = (f(Tp) - f(Tm)) / 2e-6
+        assert abs(fd - g[idx]) < 1e-7 * np.abs(g).max()
+    assert abs(float(np.sum(T0 * g)) - 1.0) < 1e-10
+    assert any(ck["side"] == 1 for ck in fwd["ckpt"])
