@@ -161,6 +161,16 @@ typedef struct {
   int chain_steps;          /* scheme 1: 1 = also evaluate lnz of every depth k < n during the
                                forward (hotrg_chain_lnz_steps: the whole cooling curve, beta_k
                                = 2^(k+1) tau, from one forward); 0 = the last depth only.  */
+  int w_rule;               /* which environment gives the isometry (SM Sec. B, "local HOSVD"):
+                               0 = the Gram matrix of the merged pair along its left bond
+                               (x1 x2), always (default); 1 = Xie2012's rule: the HOSVD along
+                               the left and along the right bond (x1' x2'), the side whose
+                               discarded eigenvalues sum to less gives w (both Gram matrices
+                               have the same trace; relative differences up to 1e-12 count as a
+                               tie, which takes the left side).  The backward differentiates
+                               through the side taken (discontinuous where the two are equal).
+                               w_rule 1 doubles the Gram and eigensolve work, uses the exact
+                               eigensolvers (eigh_mode is ignored) and needs w_given = 0.  */
 } hotrg_config;
 
 typedef struct hotrg_plan_s* hotrg_plan;
@@ -170,7 +180,7 @@ typedef struct hotrg_plan_s* hotrg_plan;
  * hi_precision_steps = 2, eigh_mode = 0, eigh_power_iters = 4, eigh_block = 0,
  * epilogue_split = 1, split_chunk_elems = 0, w_given = 0, eigh_residual_tol = 0,
  * stage2_n_group = 0, stage2_pair = 0, gemm_sm_reserve = 0, eigh_warm_start = 0,
- * scheme = 0, chain_steps = 0.
+ * scheme = 0, chain_steps = 0, w_rule = 0.
  * d0, d_cut, n_steps as given. */
 void hotrg_config_default(hotrg_config* cfg, int d0, int d_cut, int n_steps);
 
@@ -278,6 +288,10 @@ hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double 
  * as hotrg_forward_tensor. */
 hotrg_status hotrg_forward_xy(hotrg_plan plan, double tau, double J, double* lnz_per_copy,
                               double* log_norms);
+
+/* w_rule 1: the side (0 = left, 1 = right) each step of the last forward took
+ * its isometry from (host array of the steps run; all 0 for w_rule 0). */
+hotrg_status hotrg_isometry_sides(hotrg_plan plan, int* side);
 
 /* Scheme 1: lnz of every depth k = 1..n of the last forward (host array of
  * the steps run); entries before the last are NaN unless chain_steps = 1. */

@@ -32,7 +32,7 @@ EXPORTS = (
     "hotrg_plan_destroy", "hotrg_forward_tensor", "hotrg_forward_ising",
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
     "hotrg_plan_set_steps", "hotrg_plan_set_stream", "hotrg_plan_set_given_steps",
-    "hotrg_forward_xy", "hotrg_chain_lnz_steps",
+    "hotrg_forward_xy", "hotrg_chain_lnz_steps", "hotrg_isometry_sides",
     "hotrg_lbfgs_create", "hotrg_lbfgs_layer", "hotrg_lbfgs_destroy",
     "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
@@ -59,7 +59,8 @@ class hotrg_config(ctypes.Structure):
                 ("w_given", ctypes.c_int), ("eigh_residual_tol", ctypes.c_double),
                 ("stage2_n_group", ctypes.c_int), ("stage2_pair", ctypes.c_int),
                 ("gemm_sm_reserve", ctypes.c_int), ("eigh_warm_start", ctypes.c_int),
-                ("scheme", ctypes.c_int), ("chain_steps", ctypes.c_int)]
+                ("scheme", ctypes.c_int), ("chain_steps", ctypes.c_int),
+                ("w_rule", ctypes.c_int)]
 
 
 class hotrg_request(ctypes.Structure):
@@ -155,6 +156,7 @@ def lib() -> ctypes.CDLL:
     L.hotrg_plan_set_given_steps.argtypes = [vp, ctypes.c_int]
     L.hotrg_forward_xy.argtypes = [vp, ctypes.c_double, ctypes.c_double, _dp, _dp]
     L.hotrg_chain_lnz_steps.argtypes = [vp, _dp]
+    L.hotrg_isometry_sides.argtypes = [vp, _ip]
     L.hotrg_lbfgs_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
     L.hotrg_lbfgs_layer.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]
@@ -182,7 +184,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
                 w_given: bool = False, eigh_residual_tol: float = 0.0,
                 stage2_n_group: int = 0, stage2_pair: int = 0,
                 gemm_sm_reserve: int = 0, eigh_warm_start: int = 0, scheme: int = 0,
-                chain_steps: bool = False) -> hotrg_config:
+                chain_steps: bool = False, w_rule: int = 0) -> hotrg_config:
     c = hotrg_config()
     lib().hotrg_config_default(ctypes.byref(c), d0, d_cut, n_steps)
     c.precision = PRECISIONS[precision] if isinstance(precision, str) else int(precision)
@@ -205,6 +207,7 @@ def make_config(d0: int, d_cut: int, n_steps: int, precision="fp64", split_from_
     c.eigh_warm_start = int(eigh_warm_start)
     c.scheme = int(scheme)
     c.chain_steps = int(bool(chain_steps))
+    c.w_rule = int(w_rule)
     return c
 
 
@@ -233,13 +236,14 @@ class Plan:
                  epilogue_split: bool = True, split_chunk_elems: int = 0,
                  w_given: bool = False, eigh_residual_tol: float = 0.0,
                  stage2_n_group: int = 0, stage2_pair: int = 0, gemm_sm_reserve: int = 0,
-                 eigh_warm_start: int = 0, scheme: int = 0, chain_steps: bool = False):
+                 eigh_warm_start: int = 0, scheme: int = 0, chain_steps: bool = False,
+                 w_rule: int = 0):
         self.cfg = make_config(d0, d_cut, n_steps, precision, split_from_step, want_grad,
                                fixed_w_grad, eigh_broadening, gram_split_from_step,
                                hi_precision_steps, eigh_mode, eigh_power_iters, eigh_block,
                                epilogue_split, split_chunk_elems, w_given, eigh_residual_tol,
                                stage2_n_group, stage2_pair, gemm_sm_reserve, eigh_warm_start,
-                               scheme, chain_steps)
+                               scheme, chain_steps, w_rule)
         self.d0, self.d_cut, self.n_steps = d0, d_cut, n_steps
         self.n_run = n_steps
         h = ctypes.c_void_p(0)
@@ -292,6 +296,13 @@ class Plan:
         last unless the plan has chain_steps)."""
         out = np.zeros(self.n_run)
         self._check(lib().hotrg_chain_lnz_steps(self._h, _p(out)), "chain_lnz_steps")
+        return out
+
+    def isometry_sides(self):
+        """Side (0 left, 1 right) of each step's isometry in the last forward."""
+        out = np.zeros(self.n_run, dtype=np.int32)
+        self._check(lib().hotrg_isometry_sides(self._h, out.ctypes.data_as(_ip)),
+                    "isometry_sides")
         return out
 
     def set_given_steps(self, k0: int):

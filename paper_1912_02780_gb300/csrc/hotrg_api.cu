@@ -196,6 +196,11 @@ struct hotrg_plan_s {
   // (right one of the last forward, left one of the backward), power-iteration
   // buffers, and out_k of every step
   double *chR = nullptr, *chW = nullptr, *chV = nullptr, *chZ = nullptr, *lnz_steps = nullptr;
+  // w_rule 1: the right side's eigenpairs, truncation error and gap, and the
+  // side each step took (device, and read on the host by the backward)
+  double *Er = nullptr, *lamR = nullptr, *trR = nullptr;
+  int* side_dev = nullptr;
+  std::vector<int> side_host;
   std::string last_error;
   // optional per-stage CUDA-event timing
   bool prof = false;
@@ -296,6 +301,7 @@ hotrg_status validate(const hotrg_config* c) {
   if (c->scheme < 0 || c->scheme > 1 || c->chain_steps < 0 || c->chain_steps > 1)
     return HOTRG_EINVAL;
   if (c->scheme == 1 && c->d_cut > 4096) return HOTRG_EINVAL;
+  if (c->w_rule < 0 || c->w_rule > 1 || (c->w_rule == 1 && c->w_given)) return HOTRG_EINVAL;
   return HOTRG_OK;
 }
 
@@ -374,16 +380,27 @@ enum StageId { kStGram = 0, kStEigh = 1, kStS1 = 2, kStS2 = 3, kStS3 = 4, kStNor
                kStEighProd = 11, kStEighQR = 12, kStEighRR = 13, kStEighRes = 14,
                kStF64 = 16 };
 
+// Strides of T's horizontal legs l and r: the Gram matrix of the right side
+// (w_rule 1) is the left one of T with l and r exchanged, i.e. the same
+// contractions with the two strides swapped.
+void lr_strides(const StepGeom& s, bool right, long long& sl, long long& sr) {
+  const long long XY2 = (long long)s.X * s.Y * s.Y, Y2 = (long long)s.Y * s.Y;
+  sl = right ? Y2 : XY2;
+  sr = right ? XY2 : Y2;
+}
+
 hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* A, double* B,
-                      double* G) {
+                      double* G, bool right = false) {
   Stage sc(p, kStGram + kStF64);
   const int X = s.X, Y = s.Y;
   const long long XY2 = (long long)X * Y * Y, Y2 = (long long)Y * Y;
+  long long sl, sr;
+  lr_strides(s, right, sl, sr);
   cudaStream_t st = p->stream;
-  CK(gemm_f64(g64(p, T, map2(Y, 1, XY2), map2(Y, Y, Y2), T, map2(Y, 1, XY2), map2(Y, Y, Y2), A,
+  CK(gemm_f64(g64(p, T, map2(Y, 1, sl), map2(Y, Y, sr), T, map2(Y, 1, sl), map2(Y, Y, sr), A,
                   map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y, 1.0, 0.0),
               st, p->sms));
-  CK(gemm_f64(g64(p, T, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, Y, XY2), map2(Y, 1, Y2), B,
+  CK(gemm_f64(g64(p, T, map2(Y, Y, sl), map2(Y, 1, sr), T, map2(Y, Y, sl), map2(Y, 1, sr), B,
                   map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y, 1.0, 0.0),
               st, p->sms));
   if (G)
@@ -394,15 +411,18 @@ hotrg_status gram_f64(hotrg_plan p, const StepGeom& s, const double* T, double* 
   return HOTRG_OK;
 }
 
-hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double* G) {
+hotrg_status gram_split(hotrg_plan p, const StepGeom& s, const double* T, double* G,
+                        bool right = false) {
   const int X = s.X, Y = s.Y, np = s.np;
   const long long XY2 = (long long)X * Y * Y, Y2 = (long long)Y * Y;
+  long long sl, sr;
+  lr_strides(s, right, sl, sr);
   cudaStream_t st = p->stream;
   const long long sT = p->L.splitT, sG = p->L.splitG;
   {
     Stage sc(p, kStPrep);
-    CK(gsplit(p, T, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, np, sT, p->pTA));
-    CK(gsplit(p, T, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, np, sT, p->pTB));
+    CK(gsplit(p, T, map2(Y, 1, sl), map2(Y, Y, sr), X * Y, X * Y, np, sT, p->pTA));
+    CK(gsplit(p, T, map2(Y, Y, sl), map2(Y, 1, sr), X * Y, X * Y, np, sT, p->pTB));
   }
   Stage sc(p, kStGram);
   TcOperand ta = opnd(p->pTA, X * Y, X * Y, np, sT), tb = opnd(p->pTB, X * Y, X * Y, np, sT);
@@ -554,7 +574,7 @@ int subspace_k(const hotrg_config& c, const StepGeom& s) {
 }
 
 bool subspace_applies(const hotrg_config& c, const StepGeom& s) {
-  return c.eigh_mode == 1 && (!c.want_grad || c.fixed_w_grad) &&
+  return c.eigh_mode == 1 && c.w_rule == 0 && (!c.want_grad || c.fixed_w_grad) &&
          (long long)subspace_k(c, s) < s.N;
 }
 
@@ -856,6 +876,9 @@ hotrg_status chain_seed(hotrg_plan p) {
 // step to the exact partial eigensolver (one iteration costs ~10 ms at
 // D = 64, the exact solver ~350 ms).
 constexpr int kGuardMaxIters = 4;
+// w_rule 1: relative truncation errors closer than this count as a tie (left);
+// where the two sides of a tensor have the same spectrum they differ by rounding.
+constexpr double kWRuleTie = 1e-12;
 
 hotrg_status step_forward(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
@@ -944,6 +967,31 @@ hotrg_status step_forward(hotrg_plan p, int k) {
     }
     if ((r = finish(p->Escr, ncols)) != HOTRG_OK) return r;
     CK(set_value(p->dres + (k - 1), std::nan(""), nullptr, 0, st));
+    if (p->cfg.w_rule == 1 && s.Xp < N) {
+      // Xie2012: the HOSVD along the right bond too; the side that discards
+      // less (relative to the common trace) gives w, the left one on a tie
+      if (s.split && k >= p->cfg.gram_split_from_step) r = gram_split(p, s, T, p->Escr, true);
+      else r = gram_f64(p, s, T, p->Abuf, p->Bbuf, p->Escr, true);
+      if (r != HOTRG_OK) return r;
+      if (p->cfg.want_grad || s.Xp >= N) {
+        cusolverStatus_t cs = cusolverDnDsyevd(p->solver, CUSOLVER_EIG_MODE_VECTOR,
+                                               CUBLAS_FILL_MODE_LOWER, N, p->Escr, N, p->wasc,
+                                               p->work, p->lwork, p->info);
+        if (cs != CUSOLVER_STATUS_SUCCESS) return fail(p, HOTRG_ECUDA, "cusolverDnDsyevd failed");
+      } else if ((r = exact_partial()) != HOTRG_OK) {
+        return r;
+      }
+      CK(eigh_info_check(p->info, p->err, st));
+      const int rows = (p->cfg.want_grad && ncols >= N) ? N : s.Xp;
+      CK(eig_desc(p->Escr, p->wasc, N, ncols, rows, p->Er, p->lamR, st));
+      CK(eig_diag(p->lamR, ncols, N, s.Xp, p->scal + 3, p->trR, p->trR + 1, st));
+      CK(w_rule_choose(p->dtrunc + (k - 1), p->trR, kWRuleTie, p->side_dev + (k - 1), st));
+      const int* f = p->side_dev + (k - 1);
+      CK(cond_copy(f, p->Er, Ek, (long long)rows * N, st, p->sms));
+      CK(cond_copy(f, p->lamR, lk, ncols, st, p->sms));
+      CK(cond_copy(f, p->trR, p->dtrunc + (k - 1), 1, st, p->sms));
+      CK(cond_copy(f, p->trR + 1, p->dgap + (k - 1), 1, st, p->sms));
+    }
   }
   if (p->wkeep[k & 1]) {
     // this step's kept eigenvectors: the warm start of step k + 2
@@ -1105,6 +1153,8 @@ hotrg_status step_backward(hotrg_plan p, int k) {
   }
   if (!p->cfg.fixed_w_grad && Xp < N) {
     Stage sc(p, kStBwdEigh + (sp ? 0 : kStF64));
+    long long sl, sr;
+    lr_strides(s, p->side_host.size() >= (size_t)k && p->side_host[k - 1] != 0, sl, sr);
     const int nd = (int)(N - Xp);
     const double* Ud = Ek + (long long)Xp * N;
     // S[j][k] = sum_i U_d[i][j] wbar[i][k]
@@ -1122,13 +1172,13 @@ hotrg_status step_backward(hotrg_plan p, int k) {
                 st, p->sms));
     CK(symmetrize(p->Gb, (int)N, st, p->sms));
     {
-      // Gram halves again (A, B of the forward), FP64 output
+      // Gram halves again (A, B of the forward, of the side that gave w), FP64 output
       const long long XY2g = (long long)X * Y * Y, Y2g = (long long)Y * Y;
-      CK(run_gemm(p, snp, g64(p, T, map2(Y, 1, XY2g), map2(Y, Y, Y2g), T, map2(Y, 1, XY2g),
-                             map2(Y, Y, Y2g), p->Abuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
+      CK(run_gemm(p, snp, g64(p, T, map2(Y, 1, sl), map2(Y, Y, sr), T, map2(Y, 1, sl),
+                             map2(Y, Y, sr), p->Abuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
                              X * Y, X * Y, 1.0, 0.0)));
-      CK(run_gemm(p, snp, g64(p, T, map2(Y, Y, XY2g), map2(Y, 1, Y2g), T, map2(Y, Y, XY2g),
-                             map2(Y, 1, Y2g), p->Bbuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
+      CK(run_gemm(p, snp, g64(p, T, map2(Y, Y, sl), map2(Y, 1, sr), T, map2(Y, Y, sl),
+                             map2(Y, 1, sr), p->Bbuf, map2(Y, Y, XY2g), map2(Y, 1, Y2g), X * Y,
                              X * Y, X * Y, 1.0, 0.0)));
     }
     const long long X3 = X2 * X;
@@ -1137,13 +1187,13 @@ hotrg_status step_backward(hotrg_plan p, int k) {
                     p->Abar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
     CK(run_gemm(p, snp, g64(p, p->Gb, map2(X, 1, X2), map2(X, X, X3), p->Abuf, map_lin(1), map_lin(Y2),
                     p->Bbar, map_lin(Y2), map_lin(1), X * X, Y * Y, X * X, 1.0, 0.0)));
-    // Tbar[a i y j] += 2 sum_{c k} Abar[a j c k] T[c i y k]
-    CK(run_gemm(p, snp, g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, Y2),
-                    map2(Y, 1, XY2), p->Tbar, map2(Y, 1, XY2), map2(Y, Y, Y2), X * Y, X * Y, X * Y,
+    // Tbar[a i y j] += 2 sum_{c k} Abar[a j c k] T[c i y k]   (l, r strides of the side)
+    CK(run_gemm(p, snp, g64(p, p->Abar, map2(Y, Y, X * Y2), map2(Y, 1, Y2), T, map2(Y, Y, sr),
+                    map2(Y, 1, sl), p->Tbar, map2(Y, 1, sl), map2(Y, Y, sr), X * Y, X * Y, X * Y,
                     2.0, 1.0)));
     // Tbar[b k j z] += 2 sum_{d m} Bbar[b j d m] T[d k m z]
-    CK(run_gemm(p, snp, g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, Y2),
-                    map2(Y, Y, XY2), p->Tbar, map2(Y, Y, XY2), map2(Y, 1, Y2), X * Y, X * Y, X * Y,
+    CK(run_gemm(p, snp, g64(p, p->Bbar, map2(Y, Y, XY2), map2(Y, 1, Y2), T, map2(Y, 1, sr),
+                    map2(Y, Y, sl), p->Tbar, map2(Y, Y, sl), map2(Y, 1, sr), X * Y, X * Y, X * Y,
                     2.0, 1.0)));
   }
   // d(ln Z/N)/d w_k = wbT / 2^k (wbT carries the 2^k of E_k)
@@ -1160,6 +1210,12 @@ hotrg_status step_backward(hotrg_plan p, int k) {
 
 hotrg_status run_backward(hotrg_plan p) {
   const StepGeom& last = p->L.g[p->n_run - 1];
+  if (p->side_dev) {
+    p->side_host.assign(p->cfg.n_steps, 0);
+    CK(cudaMemcpyAsync(p->side_host.data(), p->side_dev, sizeof(int) * p->n_run,
+                       cudaMemcpyDeviceToHost, p->stream));
+    CK(cudaStreamSynchronize(p->stream));
+  }
   if (p->cfg.scheme == 1) {
     hotrg_status r = chain_seed(p);
     if (r != HOTRG_OK) return r;
@@ -1310,6 +1366,7 @@ void hotrg_config_default(hotrg_config* c, int d0, int d_cut, int n_steps) {
   c->eigh_warm_start = 0;
   c->scheme = 0;
   c->chain_steps = 0;
+  c->w_rule = 0;
 }
 
 hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
@@ -1350,6 +1407,10 @@ hotrg_status hotrg_plan_workspace_bytes(const hotrg_config* c, size_t* bytes) {
       b.add(kmax * L.maxN, 8 * 2);
       b.add(kmax * kmax, 8);
     }
+  }
+  if (c->w_rule == 1) {
+    b.add(L.maxN2, 8);                                    // right-side eigenvectors
+    b.add(L.maxN + c->n_steps + 4, 8);
   }
   if (c->scheme == 1) {
     const long long Xm = L.maxXp > c->d0 ? L.maxXp : c->d0;
@@ -1531,6 +1592,16 @@ hotrg_status hotrg_plan_create(const hotrg_config* cfg, void* cuda_stream, hotrg
       p->lswork = ls;
       ALC(p->swork, (long long)ls);
     }
+  }
+  if (cfg->w_rule == 1) {
+    ALC(p->Er, L.maxN2);
+    ALC(p->lamR, L.maxN);
+    ALC(p->trR, 2);
+    long long nint = (n + 1) / 2 + 1;          // n ints in doubles
+    double* sd = nullptr;
+    ALC(sd, nint);
+    p->side_dev = reinterpret_cast<int*>(sd);
+    if (cudaMemset(p->side_dev, 0, sizeof(int) * n) != cudaSuccess) return cleanup(HOTRG_ECUDA);
   }
   if (cfg->scheme == 1) {
     const long long Xm = L.maxXp > cfg->d0 ? L.maxXp : cfg->d0;
@@ -1773,6 +1844,18 @@ hotrg_status hotrg_forward_xy(hotrg_plan p, double tau, double J, double* lnz, d
   hotrg_status r = hotrg_forward_device(p, p->T[0], nullptr);
   if (r != HOTRG_OK) return r;
   return copy_out(p, lnz, log_norms, nullptr);
+}
+
+hotrg_status hotrg_isometry_sides(hotrg_plan p, int* side) {
+  if (!p || !side) return HOTRG_EINVAL;
+  if (!p->have_fwd) return fail(p, HOTRG_ESTATE, "no forward yet");
+  if (!p->side_dev) {
+    for (int k = 0; k < p->n_run; ++k) side[k] = 0;
+    return HOTRG_OK;
+  }
+  CK(cudaMemcpyAsync(side, p->side_dev, sizeof(int) * p->n_run, cudaMemcpyDeviceToHost,
+                     p->stream));
+  return finish_sync(p);
 }
 
 hotrg_status hotrg_chain_lnz_steps(hotrg_plan p, double* out) {

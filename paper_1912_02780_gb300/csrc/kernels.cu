@@ -639,6 +639,23 @@ __global__ void eye_unit_kernel(double* __restrict__ V, int X) {
   for (long long i = gtid(); i < n; i += gstride()) V[i] = (i / X == i % X) ? v : 0.0;
 }
 
+
+// w_rule 1: *side = 1 when the right side's relative truncation error is
+// smaller than the left one's by more than tie (a relative tie band: both
+// Gram matrices have the same trace).
+__global__ void w_rule_choose_kernel(const double* __restrict__ trunc_l,
+                                     const double* __restrict__ trunc_r, double tie,
+                                     int* __restrict__ side) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *side = (*trunc_l - *trunc_r > tie) ? 1 : 0;
+}
+
+// dst = src where *flag != 0 (the chosen side's eigenpairs).
+__global__ void cond_copy_kernel(const int* __restrict__ flag, const double* __restrict__ src,
+                                 double* __restrict__ dst, long long n) {
+  if (*flag == 0) return;
+  for (long long i = gtid(); i < n; i += gstride()) dst[i] = src[i];
+}
+
 }  // namespace
 
 cudaError_t gather_split(const double* src, long long src_lim, IMap rm, IMap km, int rows, int K,
@@ -851,6 +868,20 @@ cudaError_t chain_lnz(const double* log_norms, int n, const double* lnlam, doubl
 cudaError_t eye_unit(double* V, int X, cudaStream_t st, int sms) {
   count_launch();
   eye_unit_kernel<<<blocks_for((long long)X * X, sms), 256, 0, st>>>(V, X);
+  return cudaGetLastError();
+}
+
+cudaError_t w_rule_choose(const double* trunc_l, const double* trunc_r, double tie, int* side,
+                          cudaStream_t st) {
+  count_launch();
+  w_rule_choose_kernel<<<1, 32, 0, st>>>(trunc_l, trunc_r, tie, side);
+  return cudaGetLastError();
+}
+
+cudaError_t cond_copy(const int* flag, const double* src, double* dst, long long n,
+                      cudaStream_t st, int sms) {
+  count_launch();
+  cond_copy_kernel<<<blocks_for(n, sms), 256, 0, st>>>(flag, src, dst, n);
   return cudaGetLastError();
 }
 

@@ -58,6 +58,11 @@ cudaError_t diff_norm(const double* a, const double* b, long long n, double* out
 // out (if not NULL) = [v, 1, ln c_1 .. ln c_n]; *step_out (if not NULL) = v.
 cudaError_t chain_lnz(const double* log_norms, int n, const double* lnlam, double* out,
                       double* step_out, cudaStream_t st);
+// w_rule 1: *side = (*trunc_l - *trunc_r > tie); dst = src where *flag.
+cudaError_t w_rule_choose(const double* trunc_l, const double* trunc_r, double tie, int* side,
+                          cudaStream_t st);
+cudaError_t cond_copy(const int* flag, const double* src, double* dst, long long n,
+                      cudaStream_t st, int sms);
 // V = identity / sqrt(X) (X x X).
 cudaError_t eye_unit(double* V, int X, cudaStream_t st, int sms);
 
