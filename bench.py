@@ -87,11 +87,11 @@ def products_of_step(k, split_from, hi_steps, precision):
 # dram__bytes_write.sum) of the tensor-core GEMM source with this SHA-256; the
 # value is reported only while csrc/gemm_tc.cu is unchanged since the capture.
 STAGE2_TRAFFIC = {
-    "gemm_tc_sha256": "2560578679a3c54ebac416b14361e556950e92d342b88e2d0a1c9b8ede2ae711",
+    "gemm_tc_sha256": "e71848dcbe2214a6f30c74c75d170e62260694ed98df8242db7fe1e3aa06a245",
     # full-size D = 64 three-plane stage-2 launch (step 7 of the benchmark's
-    # solve: N-tile groups of 16, 136 CTAs with 16 SMs reserved), one-pass ncu
-    # capture: 59.58 GB read + 8.76 GB written
-    "bytes_per_launch_d64": 59.58e9 + 8.76e9,
+    # solve: N-tile groups of 16, 136 CTAs with 16 SMs reserved, 44.46 ms under
+    # ncu), one-pass ncu capture: 48.25 GB read + 8.67 GB written
+    "bytes_per_launch_d64": 48.25e9 + 8.67e9,
     "captured": "profiles/tc_gemm_stage2_c4_d64.md"}
 
 
@@ -427,7 +427,7 @@ def run_grid(args):
     res = ising_thermodynamics(betas, 32, 30, args.precision,
                                split_from_step=args.split_from if split else 1,
                                hi_precision_steps=args.hi_steps, concurrent=args.concurrent,
-                               sm_reserve=args.sm_reserve)
+                               sm_reserve=args.sm_reserve, grouped=args.grid_group)
     dt = time.perf_counter() - t0
     line = {"metric": "beta-grid solves/s (forward + backward)", "value": len(betas) / dt,
             "unit": "solves/s", "higher_is_better": True, "seconds": dt,
@@ -435,7 +435,8 @@ def run_grid(args):
             "config": {"workload": "c2_grid", "betas": len(betas), "d_cut": 32, "n_steps": 30,
                        "split_from_step": args.split_from if split else None,
                        "hi_precision_steps": args.hi_steps if split else None,
-                       "concurrent_plans": args.concurrent, "sm_reserve": args.sm_reserve}}
+                       "concurrent_plans": args.concurrent, "sm_reserve": args.sm_reserve,
+                       "grouped_forward": args.grid_group}}
     g = golden("c2_grid")
     if g:
         lnz_ref = np.array([q["lnz"] for q in g["points"]])
@@ -605,6 +606,69 @@ def run_lbfgs(args):
                       "hotrg_abs_err_lnz": abs(lb["lnz_hotrg"] - ons)}), flush=True)
 
 
+def run_group(args):
+    """Grouped forward against the same solves one after another and on
+    concurrent streams: G Ising solves (beta spread over [0.30, 0.60], h = 0)
+    of one shape per D_cut, BF16X6 split from step 5, forward only, subspace
+    eigensolver; solves/s of each form and the launch counts; every grouped
+    result compared with the solo one (bit for bit)."""
+    import torch
+    import paper_1912_02780_gb300 as hot
+    G, n = args.group_size, 30
+    dev = torch.device("cuda", 0)
+    betas = list(np.linspace(0.30, 0.60, G))
+    rows = []
+    for D in [int(x) for x in args.group_d.split(",")]:
+        kw = dict(split_from_step=5, want_grad=False, hi_precision_steps=2, eigh_mode=1,
+                  eigh_power_iters=2, eigh_warm_start=1)
+        st = torch.cuda.Stream(dev)
+        plans = [hot.Plan(2, D, n, "bf16x6", stream=st.cuda_stream, **kw) for _ in range(G)]
+        grp = hot.Group(2, D, n, "bf16x6", max_count=G, stream=st.cuda_stream, **kw)
+        streams = [torch.cuda.Stream(dev) for _ in range(G)]
+        cplans = [hot.Plan(2, D, n, "bf16x6", stream=s2.cuda_stream, **kw) for s2 in streams]
+        pool = ThreadPoolExecutor(max_workers=G)
+
+        def solo():
+            return [p.forward_ising(b)[0] for p, b in zip(plans, betas)]
+
+        def grouped():
+            return list(grp.forward_ising(plans, betas))
+
+        def concurrent():
+            return list(pool.map(lambda i: cplans[i].forward_ising(betas[i])[0], range(G)))
+
+        out = {"d_cut": D, "solves": G}
+        ref = None
+        for name, fn in (("solo", solo), ("grouped", grouped), ("concurrent", concurrent)):
+            for _ in range(args.warmup):
+                r = fn()
+            torch.cuda.synchronize()
+            l0 = hot.kernel_launches()
+            t0 = time.perf_counter()
+            for _ in range(args.steps):
+                r = fn()
+            torch.cuda.synchronize()
+            dt = (time.perf_counter() - t0) / args.steps
+            out[name] = {"solves_per_s": G / dt, "ms": 1e3 * dt,
+                         "launches_per_round": (hot.kernel_launches() - l0) // args.steps}
+            if ref is None:
+                ref = r
+            else:
+                out[name]["bit_identical_to_solo"] = bool(list(r) == list(ref))
+        out["grouped_launches_per_round"] = grp.launches()
+        rows.append(out)
+        print(json.dumps(out), flush=True)
+        pool.shutdown()
+        grp.close()
+        for p in plans + cplans:
+            p.close()
+    print(json.dumps({"metric": "grouped forward vs solo and concurrent solves",
+                      "config": {"model": "ising", "n_steps": n, "solves": G,
+                                 "precision": "bf16x6", "split_from_step": 5,
+                                 "eigensolver": "subspace, warm start"},
+                      "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -666,6 +730,12 @@ def main():
                     help="L-BFGS (exponential parametrisation) vs MERA update, one sweep")
     ap.add_argument("--lbfgs-d", type=int, default=16)
     ap.add_argument("--lbfgs-iters", type=int, default=5)
+    ap.add_argument("--group", action="store_true",
+                    help="grouped forward vs solo and concurrent solves at small D_cut")
+    ap.add_argument("--group-d", default="16,24,32")
+    ap.add_argument("--group-size", type=int, default=4)
+    ap.add_argument("--grid-group", type=int, default=0,
+                    help="--grid: betas per grouped forward (0: none)")
     ap.add_argument("--gemm-case", default="",
                     help="M,N,K: one three-plane split GEMM of the stage-2 kind through the "
                          "kernel-check entry point (a small case for ncu captures)")
@@ -692,6 +762,8 @@ def main():
         return run_xy(args)
     if args.lbfgs:
         return run_lbfgs(args)
+    if args.group:
+        return run_group(args)
     if args.warmup < 3:
         print("warning: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -289,6 +289,35 @@ hotrg_status hotrg_forward_ising(hotrg_plan plan, double beta, double J, double 
 hotrg_status hotrg_forward_xy(hotrg_plan plan, double tau, double J, double* lnz_per_copy,
                               double* log_norms);
 
+/* Grouped forward (the solve server's grouped launch of same-shape steps of
+ * different requests).  A group holds the batched operand buffers of one
+ * problem shape for up to max_count plans; hotrg_forward_group_* runs the
+ * forwards of `count` plans created with that config (any depths set with
+ * hotrg_plan_set_steps) in lockstep on the group's stream, which every plan
+ * must be bound to: per step each plan forms its own isometry (Gram matrix and
+ * eigensolve), then on split steps whose free leg fits one chunk the three
+ * contractions of all plans are ONE tensor-core launch per stage (each
+ * problem's operand rows at its own offset of the group's buffers), then each
+ * plan normalises; other steps run plan by plan.  Every plan ends as after its
+ * own forward (results bit-identical; hotrg_backward, diagnostics and the
+ * outputs work per plan).  T0_host: count * d0^4 float64 (plan i's tensor at
+ * i * d0^4); beta, J, h: count values; lnz (host, may be NULL): count values.
+ * Scheme 0, w_given 0 and w_rule 0 only.  Device errors of a grouped launch
+ * are reported by every plan of the call.  hotrg_group_launches: grouped
+ * launches issued so far. */
+typedef struct hotrg_group_s* hotrg_group;
+hotrg_status hotrg_group_create(const hotrg_config* cfg, int max_count, void* cuda_stream,
+                                hotrg_group* out);
+hotrg_status hotrg_forward_group_tensor(hotrg_group group, hotrg_plan* plans, int count,
+                                        const double* T0_host, double* lnz_per_site);
+hotrg_status hotrg_forward_group_ising(hotrg_group group, hotrg_plan* plans, int count,
+                                       const double* beta, const double* J, const double* h,
+                                       double* lnz_per_site);
+unsigned long long hotrg_group_launches(hotrg_group group);
+/* Device bytes hotrg_group_create would allocate (for admission control). */
+hotrg_status hotrg_group_workspace_bytes(const hotrg_config* cfg, int max_count, size_t* bytes);
+void hotrg_group_destroy(hotrg_group group);
+
 /* w_rule 1: the side (0 = left, 1 = right) each step of the last forward took
  * its isometry from (host array of the steps run; all 0 for w_rule 0). */
 hotrg_status hotrg_isometry_sides(hotrg_plan plan, int* side);
@@ -371,7 +400,12 @@ hotrg_status hotrg_device_supports_split(void);
  * request's own depth); idle ones are freed, coldest first, when a new plan
  * would not fit, and a slot waits for a running request's plan when all
  * pooled plans are in use.  A request whose plan alone exceeds the budget
- * finishes with status HOTRG_ENOMEM.  Requests without gradients use the
+ * finishes with status HOTRG_ENOMEM.  Under backlog (every other slot busy),
+ * forward-only split-precision requests with D_cut <= 32 that are queued
+ * together (up to 4 of one D_cut, precision and split step) are taken by one
+ * slot and run as one grouped forward
+ * (hotrg_forward_group_ising: their contractions one tensor-core launch per
+ * stage; each result bit-identical to the request's own solve).  Requests without gradients use the
  * randomized subspace eigensolver (eigh_mode 1, 2 power iterations).  Times are seconds since the server was
  * created.  Submit, poll, wait, drain and stats are thread-safe. */
 typedef struct hotrg_server_s* hotrg_server;
@@ -394,6 +428,8 @@ typedef struct {
   size_t bytes_in_use, peak_bytes;
   int queue_depth, busy_slots;
   uint64_t admission_waits;  /* requests that waited for device memory before their plan */
+  uint64_t grouped;          /* requests run in a grouped forward with others */
+  uint64_t groups;           /* grouped forwards run */
 } hotrg_server_stats;
 hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_server* out);
 hotrg_status hotrg_server_submit(hotrg_server server, const hotrg_request* req, uint64_t* ticket);

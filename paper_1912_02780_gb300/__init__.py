@@ -33,6 +33,8 @@ EXPORTS = (
     "hotrg_forward_device", "hotrg_backward", "hotrg_backward_device", "hotrg_sync",
     "hotrg_plan_set_steps", "hotrg_plan_set_stream", "hotrg_plan_set_given_steps",
     "hotrg_forward_xy", "hotrg_chain_lnz_steps", "hotrg_isometry_sides",
+    "hotrg_group_create", "hotrg_forward_group_tensor", "hotrg_forward_group_ising",
+    "hotrg_group_launches", "hotrg_group_destroy", "hotrg_group_workspace_bytes",
     "hotrg_lbfgs_create", "hotrg_lbfgs_layer", "hotrg_lbfgs_destroy",
     "hotrg_diagnostics", "hotrg_eigh_diagnostics", "hotrg_step_dims", "hotrg_status_string", "hotrg_last_error",
     "hotrg_device_supports_split", "hotrg_gemm_split_check", "hotrg_gemm_f64_check",
@@ -81,7 +83,8 @@ class hotrg_server_stats(ctypes.Structure):
                 ("failed", ctypes.c_uint64), ("plans_created", ctypes.c_uint64),
                 ("plans_evicted", ctypes.c_uint64), ("bytes_in_use", ctypes.c_size_t),
                 ("peak_bytes", ctypes.c_size_t), ("queue_depth", ctypes.c_int),
-                ("busy_slots", ctypes.c_int), ("admission_waits", ctypes.c_uint64)]
+                ("busy_slots", ctypes.c_int), ("admission_waits", ctypes.c_uint64),
+                ("grouped", ctypes.c_uint64), ("groups", ctypes.c_uint64)]
 
 
 class HotrgError(RuntimeError):
@@ -147,7 +150,8 @@ def lib() -> ctypes.CDLL:
     for name in EXPORTS:
         if name not in ("hotrg_plan_destroy", "hotrg_config_default", "hotrg_status_string",
                         "hotrg_last_error", "hotrg_kernel_launches", "hotrg_server_destroy",
-                        "hotrg_config_sizeof", "hotrg_lbfgs_destroy"):
+                        "hotrg_config_sizeof", "hotrg_lbfgs_destroy", "hotrg_group_launches",
+                        "hotrg_group_destroy"):
             getattr(L, name).restype = ctypes.c_int
     L.hotrg_isometries.argtypes = [vp, _dp]
     L.hotrg_set_isometries.argtypes = [vp, _dp]
@@ -157,6 +161,17 @@ def lib() -> ctypes.CDLL:
     L.hotrg_forward_xy.argtypes = [vp, ctypes.c_double, ctypes.c_double, _dp, _dp]
     L.hotrg_chain_lnz_steps.argtypes = [vp, _dp]
     L.hotrg_isometry_sides.argtypes = [vp, _ip]
+    L.hotrg_group_create.argtypes = [ctypes.POINTER(hotrg_config), ctypes.c_int, vp,
+                                     ctypes.POINTER(vp)]
+    L.hotrg_forward_group_tensor.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, _dp, _dp]
+    L.hotrg_forward_group_ising.argtypes = [vp, ctypes.POINTER(vp), ctypes.c_int, _dp, _dp, _dp,
+                                            _dp]
+    L.hotrg_group_launches.argtypes = [vp]
+    L.hotrg_group_launches.restype = ctypes.c_ulonglong
+    L.hotrg_group_workspace_bytes.argtypes = [ctypes.POINTER(hotrg_config), ctypes.c_int,
+                                              ctypes.POINTER(ctypes.c_size_t)]
+    L.hotrg_group_destroy.argtypes = [vp]
+    L.hotrg_group_destroy.restype = None
     L.hotrg_lbfgs_create.argtypes = [vp, ctypes.c_int, ctypes.POINTER(vp)]
     L.hotrg_lbfgs_layer.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_double,
                                     ctypes.c_double, ctypes.c_int, _dp, _ip, _ip]
@@ -415,6 +430,68 @@ class Plan:
             self.close()
         except Exception:
             pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+class Group:
+    """Grouped forward of several plans of one shape (see include/hotrg.h:
+    hotrg_group_*): the same keyword arguments as ``Plan`` describe the
+    shape; every plan passed to it must be created with them and bound to the
+    same stream."""
+
+    def __init__(self, d0: int, d_cut: int, n_steps: int, precision="fp64", max_count: int = 8,
+                 stream: Optional[int] = None, **kw):
+        self.cfg = make_config(d0, d_cut, n_steps, precision, **kw)
+        self.d0 = d0
+        h = ctypes.c_void_p(0)
+        s = lib().hotrg_group_create(ctypes.byref(self.cfg), int(max_count),
+                                     ctypes.c_void_p(stream or 0), ctypes.byref(h))
+        if s:
+            raise HotrgError(s, "hotrg_group_create")
+        self._h = h
+
+    @staticmethod
+    def _handles(plans):
+        arr = (ctypes.c_void_p * len(plans))()
+        for i, p in enumerate(plans):
+            arr[i] = p._h.value
+        return arr
+
+    def _check(self, s, plans, what):
+        if s:
+            msg = lib().hotrg_last_error(plans[0]._h) if plans else b""
+            raise HotrgError(s, f"{what}: {msg.decode() if msg else ''}")
+
+    def forward_tensor(self, plans, T0s):
+        T0 = np.ascontiguousarray(np.asarray(T0s, dtype=np.float64).reshape(len(plans), -1))
+        lnz = np.zeros(len(plans))
+        self._check(lib().hotrg_forward_group_tensor(self._h, self._handles(plans), len(plans),
+                                                     _p(T0), _p(lnz)), plans, "forward_group")
+        return lnz
+
+    def forward_ising(self, plans, betas, J=1.0, h=0.0):
+        n = len(plans)
+        b = np.ascontiguousarray(np.broadcast_to(np.asarray(betas, dtype=np.float64), (n,)))
+        jj = np.ascontiguousarray(np.broadcast_to(np.asarray(J, dtype=np.float64), (n,)))
+        hh = np.ascontiguousarray(np.broadcast_to(np.asarray(h, dtype=np.float64), (n,)))
+        lnz = np.zeros(n)
+        self._check(lib().hotrg_forward_group_ising(self._h, self._handles(plans), n, _p(b),
+                                                    _p(jj), _p(hh), _p(lnz)),
+                    plans, "forward_group_ising")
+        return lnz
+
+    def launches(self) -> int:
+        return int(lib().hotrg_group_launches(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().hotrg_group_destroy(self._h)
+            self._h = ctypes.c_void_p(0)
 
     def __enter__(self):
         return self

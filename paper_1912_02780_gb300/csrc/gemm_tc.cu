@@ -561,7 +561,10 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
   auto lead = [&](uint32_t bar) { return CG == 2 ? map_to_rank(bar, 0) : bar; };
 
   // CG = 2: a tile is 2 BM rows; the pair (cluster) walks the tiles together
-  const int MT = (p.M + BM * CG - 1) / (BM * CG), NT = (p.N + BN - 1) / BN;
+  // grouped launch: MTp row tiles per problem (its rows padded to a_pitch)
+  const int bt = p.batch > 1 ? p.batch : 1;
+  const int MTp = bt > 1 ? p.a_pitch / (BM * CG) : (p.M + BM * CG - 1) / (BM * CG);
+  const int MT = MTp * bt, NT = (p.N + BN - 1) / BN;
   const long long t0 = blockIdx.x / CG, tstep = gridDim.x / CG;
   const long long tiles = (long long)MT * NT;
   const int KB = (p.K + BK - 1) / BK;
@@ -581,7 +584,9 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
       for (long long t = t0; t < tiles && ok; t += tstep) {
         int mt, nt;
         tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
-        const int arow = mt * BM * CG + (int)rank * BM, brow = nt * BN + (int)rank * C::kBRows;
+        const int bi = bt > 1 ? mt / MTp : 0;
+        const int arow = mt * BM * CG + (int)rank * BM,
+                  brow = nt * BN + (int)rank * C::kBRows + bi * p.b_pitch;
         for (int kb = 0; kb < KB; ++kb) {
           if (!mbar_wait(empty_bar(s), ph ^ 1u, p.err)) { ok = false; break; }
           if constexpr (CG == 2) {
@@ -694,10 +699,11 @@ __global__ void __launch_bounds__(Cfg<BN, NP, BK, CG>::kThreads, 1)
     for (long long t = t0; t < tiles && ok; t += tstep) {
       int mt, nt;
       tile_coords(t, MT, NT, p.m_fast, p.n_group, mt, nt);
-      const int m0 = mt * BM * CG + (int)rank * BM, n0 = nt * BN;
+      const int bi = bt > 1 ? mt / MTp : 0;
+      const int m0 = (mt - bi * MTp) * BM * CG + (int)rank * BM, n0 = nt * BN;
       const int m = m0 + row;
       const bool mok = m < p.M;
-      const long long coff = mok ? imap(p.cm, m) : 0;
+      const long long coff = mok ? imap(p.cm, m) + bi * p.c_batch : 0;
       for (int c = 0; c < nchunks; ++c) {
         // warp-uniform wait: a lane that gave up stops its whole warp
         const bool w_ok = __all_sync(0xffffffffu, mbar_wait(tfull_bar(acc), acc_ph, p.err));
@@ -956,8 +962,15 @@ cudaError_t launch(const TcOperand& A, const TcOperand& B, const TcGemm& g, cuda
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  const long long tiles =
-      (long long)((g.M + BM * CG - 1) / (BM * CG)) * ((g.N + BN - 1) / BN);
+  long long mtiles = (g.M + BM * CG - 1) / (BM * CG);
+  if (g.batch > 1) {
+    if (g.a_pitch % (BM * CG) != 0 || g.a_pitch < g.M || g.b_pitch < g.N ||
+        (long long)A.rows < (long long)g.batch * g.a_pitch ||
+        (long long)B.rows < (long long)(g.batch - 1) * g.b_pitch + g.N)
+      return cudaErrorInvalidValue;
+    mtiles = (long long)g.batch * (g.a_pitch / (BM * CG));
+  }
+  const long long tiles = mtiles * ((g.N + BN - 1) / BN);
   count_launch();
   if constexpr (CG == 1) {
     int grid = (int)(tiles < num_sms ? tiles : num_sms);

@@ -47,6 +47,13 @@ struct TcGemm {
   int cta_pair;              // 1: run a three-plane, 64-wide-K, N > 64 GEMM on CTA pairs
                              // (tcgen05 cta_group::2, 256-row tiles); same results
   int seg_prow, seg_phalf;   // kOutGridSplit: segment partner of (row, half)
+  int batch;                 // > 1: that many independent problems of this shape in one launch
+                             // (a grouped launch): problem b reads A rows from b * a_pitch and
+                             // B rows from b * b_pitch and writes at C + b * c_batch (plus the
+                             // cm / cn offsets); a_pitch a multiple of the row tile, >= M;
+                             // b_pitch >= N.  0 or 1: one problem.
+  int a_pitch, b_pitch;
+  long long c_batch;
 };
 
 // Set the products of a precision: all plane pairs (i, j) with

@@ -252,6 +252,13 @@ hotrg_status fail(hotrg_plan p, hotrg_status s, const std::string& msg) {
       return fail(p, HOTRG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+#define CK2(plan, call)                                                             \
+  do {                                                                              \
+    cudaError_t e_ = (call);                                                        \
+    if (e_ != cudaSuccess)                                                          \
+      return fail(plan, HOTRG_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
 template <typename T>
 hotrg_status dalloc(hotrg_plan p, T** ptr, long long elems) {
   *ptr = nullptr;
@@ -880,11 +887,14 @@ constexpr int kGuardMaxIters = 4;
 // where the two sides of a tensor have the same spectrum they differ by rounding.
 constexpr double kWRuleTie = 1e-12;
 
-hotrg_status step_forward(hotrg_plan p, int k) {
+// One forward step in three phases (the grouped forward runs each phase for
+// every plan of a group, with the contractions of all plans in one launch per
+// stage): the isometry (Gram matrix and eigensolve, or the given one), the
+// three contractions, and the normalisation.
+hotrg_status step_eigh(hotrg_plan p, int k) {
   const StepGeom& s = p->L.g[k - 1];
   cudaStream_t st = p->stream;
   const double* T = p->T[k - 1];
-  double* Tout = p->T[k];
   double* Ek = E_of(p, k);
   double* lk = p->lam[k - 1];
   const int N = (int)s.N;
@@ -1002,9 +1012,19 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   }
   }
   }
-  if (s.split) r = contract_split(p, s, T, Ek, Tout);
-  else r = contract_f64(p, s, T, Ek, Tout);
-  if (r != HOTRG_OK) return r;
+  return HOTRG_OK;
+}
+
+hotrg_status step_contract(hotrg_plan p, int k) {
+  const StepGeom& s = p->L.g[k - 1];
+  if (s.split) return contract_split(p, s, p->T[k - 1], E_of(p, k), p->T[k]);
+  return contract_f64(p, s, p->T[k - 1], E_of(p, k), p->T[k]);
+}
+
+hotrg_status step_finish(hotrg_plan p, int k) {
+  const StepGeom& s = p->L.g[k - 1];
+  cudaStream_t st = p->stream;
+  double* Tout = p->T[k];
   const long long n_out = (long long)s.Y * s.Y * s.Xp * s.Xp;
   if (g_inj_what.load() == kInjNaN && g_inj_arg.load() == k)
     CK(set_value(Tout, std::nan(""), nullptr, 0, st));
@@ -1022,7 +1042,14 @@ hotrg_status step_forward(hotrg_plan p, int k) {
   return HOTRG_OK;
 }
 
-hotrg_status run_forward(hotrg_plan p) {
+hotrg_status step_forward(hotrg_plan p, int k) {
+  hotrg_status r = step_eigh(p, k);
+  if (r == HOTRG_OK) r = step_contract(p, k);
+  if (r == HOTRG_OK) r = step_finish(p, k);
+  return r;
+}
+
+hotrg_status forward_begin(hotrg_plan p) {
   cudaStream_t st = p->stream;
   if (p->cfg.w_given && std::min(p->given_steps, p->n_run) > p->w_valid)
     return fail(p, HOTRG_ESTATE, "w_given plan: load the isometries first");
@@ -1031,10 +1058,23 @@ hotrg_status run_forward(hotrg_plan p) {
   p->wkeep_n[0] = p->wkeep_n[1] = 0;   // no warm start across forwards
   p->exact_step.assign(p->cfg.n_steps, 0);
   if (p->lnz_steps) CK(cudaMemsetAsync(p->lnz_steps, 0xff, sizeof(double) * p->cfg.n_steps, st));
+  return HOTRG_OK;
+}
+
+hotrg_status forward_end(hotrg_plan p);
+
+hotrg_status run_forward(hotrg_plan p) {
+  hotrg_status r = forward_begin(p);
+  if (r != HOTRG_OK) return r;
   for (int k = 1; k <= p->n_run; ++k) {
-    hotrg_status r = step_forward(p, k);
+    r = step_forward(p, k);
     if (r != HOTRG_OK) return r;
   }
+  return forward_end(p);
+}
+
+hotrg_status forward_end(hotrg_plan p) {
+  cudaStream_t st = p->stream;
   // steps past given_steps of a w_given plan have just formed their isometries
   if (p->cfg.w_given && p->n_run > p->w_valid) p->w_valid = p->n_run;
   if (p->cfg.scheme == 1) return chain_value(p, p->n_run);
@@ -1245,6 +1285,256 @@ hotrg_status finish_sync(hotrg_plan p) {
   int w[2] = {0, 0};
   CK(cudaMemcpy(w, p->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   return device_status(p, w);
+}
+
+
+// ---- grouped forward -------------------------------------------------------
+//
+// Several plans of the same shape run their forwards in lockstep on one
+// stream: per step, each plan forms its isometry (Gram matrix, eigensolve),
+// then the three contractions of all plans go out as ONE grouped tensor-core
+// launch per stage (TcGemm::batch: problem b's operand rows at b * pitch of
+// the group's buffers), then each plan normalises.  The group owns the batched
+// operand buffers ([plane][problem][rows][K], each problem's rows padded to the
+// 128-row tile where it is the first operand).  Results are bit-identical to
+// each plan's own forward: the same kernels do the same arithmetic per problem.
+
+struct GroupGeom {
+  long long pW1, pT1, pP, pW3, pU, pV, pT;   // per-problem elements (padded rows x K)
+  int aW1, aU, aV;                           // padded first-operand rows
+};
+
+GroupGeom group_geom(const StepGeom& s) {
+  const long long X = s.X, Y = s.Y, Xp = s.Xp;
+  GroupGeom g;
+  g.aW1 = (int)round_up(Xp * X, 128);
+  g.aU = (int)round_up(Y * X * Xp, 128);
+  g.aV = (int)round_up(Y * Xp * Y, 128);
+  g.pW1 = (long long)g.aW1 * X;
+  g.pT1 = Y * X * Y * X;
+  g.pP = Y * X * X * Y;
+  g.pW3 = Xp * X * X;
+  g.pU = (long long)g.aU * X * Y;
+  g.pV = (long long)g.aV * X * X;
+  g.pT = Y * Y * Xp * Xp;
+  return g;
+}
+
+// A split step the group can run as grouped launches: the whole free leg in
+// one chunk (small bond dimensions), so that every stage is one GEMM per plan.
+bool groupable(const StepGeom& s) { return s.split && s.ycs >= s.Y; }
+
+}  // namespace
+
+struct hotrg_group_s {
+  Layout L;
+  int max_count = 0, np = 0;
+  long long sW1 = 0, sT1 = 0, sP = 0, sW3 = 0, sU = 0, sV = 0, nT = 0, nF = 0;  // plane strides
+  cudaStream_t stream = nullptr;
+  std::vector<void*> allocs;
+  __nv_bfloat16 *W1 = nullptr, *T1 = nullptr, *P = nullptr, *W3 = nullptr, *U = nullptr,
+                *V = nullptr;
+  float* F32 = nullptr;
+  double* F64 = nullptr;
+  double* Tg = nullptr;
+  unsigned long long grouped_launches = 0;
+};
+
+namespace {
+
+TcOperand gopnd(const __nv_bfloat16* ptr, int count, int pitch_rows, int K, int np,
+                long long stride) {
+  return opnd(ptr, count * pitch_rows, K, np, stride);
+}
+
+// The three contractions of step k of every plan in `ps` as one grouped launch
+// per stage (mirrors contract_split for a single chunk).
+hotrg_status contract_split_group(hotrg_group g, hotrg_plan* ps, int cnt, int k) {
+  hotrg_plan p = ps[0];
+  const StepGeom& s = p->L.g[k - 1];
+  const int X = s.X, Y = s.Y, Xp = s.Xp, np = s.np;
+  const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
+  const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X;
+  cudaStream_t st = g->stream;
+  const GroupGeom gg = group_geom(s);
+  for (int i = 0; i < cnt; ++i) {
+    hotrg_plan q = ps[i];
+    Stage sc(q, kStPrep);
+    const double* Ek = E_of(q, k);
+    const double* T = q->T[k - 1];
+    CK(gsplit(q, Ek, map2(X, 1, N), map_lin(X), Xp * X, X, np, g->sW1, g->W1 + i * gg.pW1));
+    CK(gsplit(q, T, map3(Y, X, 1, Y2, Y), map_lin(XY2), Y * X * Y, X, np, g->sT1,
+              g->T1 + i * gg.pT1));
+    CK(gsplit(q, T, map2(X, Y2, 1), map2(Y, Y, XY2), Y * X, X * Y, np, g->sP, g->P + i * gg.pP));
+    CK(gsplit(q, Ek, map_lin(N), map_lin(1), Xp, X * X, np, g->sW3, g->W3 + i * gg.pW3));
+  }
+  const bool fuse = np == 3 && p->cfg.epilogue_split != 0;
+  int p1r = 0, p1h = 0, p2r = 0, p2h = 0;
+  const bool fuse1 = fuse && (Xp * X) % 128 == 0 && (XY % 128) == 0 && X % 2 == 0 &&
+                     seg_partner(Y, 1, p1r, p1h);
+  const bool fuse2 = fuse && (Y * X) % 128 == 0 && (X2 % 128) == 0 && seg_partner(X, Xp, p2r, p2h);
+  auto staged = [&](int npl) -> void* {
+    return npl == 4 ? static_cast<void*>(g->F64) : static_cast<void*>(g->F32);
+  };
+  auto batch = [&](TcGemm& t, int a_pitch, int b_pitch, long long c_batch, long long c_lim) {
+    t.batch = cnt;
+    t.a_pitch = a_pitch;
+    t.b_pitch = b_pitch;
+    t.c_batch = c_batch;
+    t.c_lim = c_lim;
+  };
+  // S1: U[(y x1' a)][(x2 j)] of every plan
+  {
+    Stage sc(p, kStS1);
+    TcGemm g1 = tcg(p, np, Xp * X, Y * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
+                    fuse1 ? kOutGridSplit : stage_mode(np), fuse1 ? (void*)g->U : staged(np),
+                    fuse1 ? g->sU : 0);
+    g1.m_fast = 1;
+    g1.seg_prow = p1r;
+    g1.seg_phalf = p1h;
+    batch(g1, gg.aW1, Y * X * Y, gg.pU, fuse1 ? g->sU : g->nF);
+    CK(tc_gemm(gopnd(g->W1, cnt, gg.aW1, X, np, g->sW1), gopnd(g->T1, cnt, Y * X * Y, X, np, g->sT1),
+               g1, st, p->tc_sms));
+    ++g->grouped_launches;
+    if (!fuse1)
+      for (int i = 0; i < cnt; ++i) {
+        const long long off = i * gg.pU;
+        if (np == 4)
+          CK(grid_split(g->F64 + off, g->nF - off, map_lin(XY), map_lin(1), Y * X * Xp, X * Y,
+                        np, g->sU, g->U + off, p->err, st, p->sms));
+        else
+          CK(grid_split(g->F32 + off, g->nF - off, map_lin(XY), map_lin(1), Y * X * Xp, X * Y,
+                        np, g->sU, g->U + off, p->err, st, p->sms));
+      }
+  }
+  // S2: V[(y a y')][(x1' x2')] of every plan
+  {
+    Stage sc(p, np == 4 ? kStS2Hi : kStS2);
+    TcGemm g2 = tcg(p, np, Y * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
+                    map2(X, 1, X2), fuse2 ? kOutGridSplit : stage_mode(np),
+                    fuse2 ? (void*)g->V : staged(np), fuse2 ? g->sV : 0);
+    g2.seg_prow = p2r;
+    g2.seg_phalf = p2h;
+    g2.n_group = stage2_group(p->cfg);
+    batch(g2, gg.aU, Y * X, gg.pV, fuse2 ? g->sV : g->nF);
+    CK(tc_gemm(gopnd(g->U, cnt, gg.aU, X * Y, np, g->sU), gopnd(g->P, cnt, Y * X, X * Y, np, g->sP),
+               g2, st, p->tc_sms));
+    ++g->grouped_launches;
+    if (!fuse2)
+      for (int i = 0; i < cnt; ++i) {
+        const long long off = i * gg.pV;
+        if (np == 4)
+          CK(grid_split(g->F64 + off, g->nF - off, map_lin(X2), map_lin(1), Y * Xp * Y, X * X,
+                        np, g->sV, g->V + off, p->err, st, p->sms));
+        else
+          CK(grid_split(g->F32 + off, g->nF - off, map_lin(X2), map_lin(1), Y * Xp * Y, X * X,
+                        np, g->sV, g->V + off, p->err, st, p->sms));
+      }
+  }
+  // S3: T'[y][y'][a][b] of every plan into the group's buffer, then home
+  {
+    Stage sc(p, kStS3);
+    TcGemm g3 = tcg(p, np, Y * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1),
+                    kOutF64, g->Tg, 0);
+    batch(g3, gg.aV, Xp, gg.pT, g->nT);
+    CK(tc_gemm(gopnd(g->V, cnt, gg.aV, X * X, np, g->sV), gopnd(g->W3, cnt, Xp, X * X, np, g->sW3),
+               g3, st, p->tc_sms));
+    ++g->grouped_launches;
+    for (int i = 0; i < cnt; ++i)
+      CK(cudaMemcpyAsync(ps[i]->T[k], g->Tg + i * gg.pT, sizeof(double) * gg.pT,
+                         cudaMemcpyDeviceToDevice, st));
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status group_check(hotrg_group g, hotrg_plan* ps, int cnt) {
+  if (!g || !ps || cnt < 1 || cnt > g->max_count) return HOTRG_EINVAL;
+  for (int i = 0; i < cnt; ++i) {
+    hotrg_plan q = ps[i];
+    if (!q) return HOTRG_EINVAL;
+    if (q->stream != g->stream)
+      return fail(q, HOTRG_EINVAL, "grouped forward: every plan must be on the group's stream");
+    if (q->cfg.scheme != 0 || q->cfg.w_given || q->cfg.w_rule != 0 ||
+        q->L.g.size() != g->L.g.size() || q->cfg.epilogue_split != ps[0]->cfg.epilogue_split ||
+        q->cfg.stage2_n_group != ps[0]->cfg.stage2_n_group ||
+        q->cfg.gemm_sm_reserve != ps[0]->cfg.gemm_sm_reserve)
+      return fail(q, HOTRG_EINVAL, "grouped forward: plan shape differs from the group's");
+    for (size_t j = 0; j < g->L.g.size(); ++j) {
+      const StepGeom &a = q->L.g[j], &b = g->L.g[j];
+      if (a.X != b.X || a.Y != b.Y || a.Xp != b.Xp || a.split != b.split || a.np != b.np ||
+          a.ycs != b.ycs)
+        return fail(q, HOTRG_EINVAL, "grouped forward: plan shape differs from the group's");
+    }
+    for (int j = 0; j < i; ++j)
+      if (ps[j] == q) return fail(q, HOTRG_EINVAL, "grouped forward: a plan appears twice");
+  }
+  return HOTRG_OK;
+}
+
+// Lockstep forward of the plans (T0 already in each plan's T[0]).
+hotrg_status group_run(hotrg_group g, hotrg_plan* ps, int cnt) {
+  int kmax = 0;
+  for (int i = 0; i < cnt; ++i) {
+    hotrg_plan q = ps[i];
+    q->have_fwd = false;
+    CK2(q, cudaMemsetAsync(q->err, 0, 3 * sizeof(int), q->stream));
+    hotrg_status r = forward_begin(q);
+    if (r != HOTRG_OK) return r;
+    kmax = std::max(kmax, q->n_run);
+  }
+  std::vector<hotrg_plan> act;
+  for (int k = 1; k <= kmax; ++k) {
+    act.clear();
+    for (int i = 0; i < cnt; ++i)
+      if (ps[i]->n_run >= k) act.push_back(ps[i]);
+    for (hotrg_plan q : act) {
+      hotrg_status r = step_eigh(q, k);
+      if (r != HOTRG_OK) return r;
+    }
+    if (act.size() > 1 && groupable(g->L.g[k - 1])) {
+      hotrg_status r = contract_split_group(g, act.data(), (int)act.size(), k);
+      if (r != HOTRG_OK) return r;
+    } else {
+      for (hotrg_plan q : act) {
+        hotrg_status r = step_contract(q, k);
+        if (r != HOTRG_OK) return r;
+      }
+    }
+    for (hotrg_plan q : act) {
+      hotrg_status r = step_finish(q, k);
+      if (r != HOTRG_OK) return r;
+    }
+  }
+  for (int i = 0; i < cnt; ++i) {
+    hotrg_status r = forward_end(ps[i]);
+    if (r != HOTRG_OK) return r;
+  }
+  // grouped launches report device errors in the first plan's error word
+  CK2(ps[0], cudaStreamSynchronize(g->stream));
+  int w0[2] = {0, 0};
+  CK2(ps[0], cudaMemcpy(w0, ps[0]->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+  for (int i = 0; i < cnt; ++i) {
+    int w[2] = {0, 0};
+    CK2(ps[i], cudaMemcpy(w, ps[i]->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
+    w[0] |= w0[0];
+    if (!w[1]) w[1] = w0[1];
+    hotrg_status r = device_status(ps[i], w);
+    if (r != HOTRG_OK) return r;
+  }
+  for (int i = 0; i < cnt; ++i) {
+    ps[i]->have_fwd = true;
+    ps[i]->fwd_ising = false;
+  }
+  return HOTRG_OK;
+}
+
+hotrg_status group_outputs(hotrg_plan* ps, int cnt, double* lnz) {
+  for (int i = 0; i < cnt; ++i) {
+    double v = 0;
+    CK2(ps[i], cudaMemcpy(&v, ps[i]->out, sizeof(double), cudaMemcpyDeviceToHost));
+    if (lnz) lnz[i] = v;
+  }
+  return HOTRG_OK;
 }
 
 }  // namespace
@@ -1844,6 +2134,131 @@ hotrg_status hotrg_forward_xy(hotrg_plan p, double tau, double J, double* lnz, d
   hotrg_status r = hotrg_forward_device(p, p->T[0], nullptr);
   if (r != HOTRG_OK) return r;
   return copy_out(p, lnz, log_norms, nullptr);
+}
+
+// Buffer sizes of a group (per-plane strides, staging and output elements).
+void group_sizes(hotrg_group_s* g) {
+  long long mW1 = 0, mT1 = 0, mP = 0, mW3 = 0, mU = 0, mV = 0, mT = 0;
+  int np = 0;
+  for (const StepGeom& s : g->L.g) {
+    if (!groupable(s)) continue;
+    const GroupGeom gg = group_geom(s);
+    np = std::max(np, s.np);
+    mW1 = std::max(mW1, gg.pW1); mT1 = std::max(mT1, gg.pT1); mP = std::max(mP, gg.pP);
+    mW3 = std::max(mW3, gg.pW3); mU = std::max(mU, gg.pU); mV = std::max(mV, gg.pV);
+    mT = std::max(mT, gg.pT);
+  }
+  g->np = np;
+  const long long c = g->max_count;
+  g->sW1 = round_up(c * mW1, 64); g->sT1 = round_up(c * mT1, 64); g->sP = round_up(c * mP, 64);
+  g->sW3 = round_up(c * mW3, 64); g->sU = round_up(c * mU, 64); g->sV = round_up(c * mV, 64);
+  g->nT = c * mT;
+  g->nF = c * std::max(mU, mV);
+}
+
+long long group_bytes(const hotrg_group_s* g) {
+  if (g->np == 0) return 0;
+  return 2LL * g->np * (g->sW1 + g->sT1 + g->sP + g->sW3 + g->sU + g->sV) + 4 * g->nF +
+         (g->L.any_hi ? 8 * g->nF : 0) + 8 * g->nT;
+}
+
+hotrg_status hotrg_group_workspace_bytes(const hotrg_config* cfg, int max_count, size_t* bytes) {
+  if (!bytes || validate(cfg) != HOTRG_OK || max_count < 1 || max_count > 64) return HOTRG_EINVAL;
+  hotrg_group_s g;
+  if (!build_layout(*cfg, g.L)) return HOTRG_EINVAL;
+  g.max_count = max_count;
+  group_sizes(&g);
+  *bytes = (size_t)group_bytes(&g);
+  return HOTRG_OK;
+}
+
+hotrg_status hotrg_group_create(const hotrg_config* cfg, int max_count, void* cuda_stream,
+                                hotrg_group* out) {
+  if (!out) return HOTRG_EINVAL;
+  *out = nullptr;
+  if (validate(cfg) != HOTRG_OK || max_count < 1 || max_count > 64) return HOTRG_EINVAL;
+  if (cfg->scheme != 0 || cfg->w_given || cfg->w_rule != 0) return HOTRG_EINVAL;
+  hotrg_group g = new hotrg_group_s();
+  if (!build_layout(*cfg, g->L)) {
+    delete g;
+    return HOTRG_EINVAL;
+  }
+  g->max_count = max_count;
+  g->stream = reinterpret_cast<cudaStream_t>(cuda_stream);
+  group_sizes(g);
+  const int np = g->np;
+  auto alloc = [&](long long bytes, void** ptr) -> bool {
+    if (bytes <= 0) { *ptr = nullptr; return true; }
+    if (cudaMalloc(ptr, (size_t)bytes) != cudaSuccess) return false;
+    g->allocs.push_back(*ptr);
+    return true;
+  };
+  bool ok = true;
+  if (np > 0) {
+    void* v;
+    ok = ok && alloc(2 * np * g->sW1, &v); g->W1 = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(2 * np * g->sT1, &v); g->T1 = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(2 * np * g->sP, &v); g->P = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(2 * np * g->sW3, &v); g->W3 = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(2 * np * g->sU, &v); g->U = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(2 * np * g->sV, &v); g->V = static_cast<__nv_bfloat16*>(v);
+    ok = ok && alloc(4 * g->nF, &v); g->F32 = static_cast<float*>(v);
+    if (g->L.any_hi) { ok = ok && alloc(8 * g->nF, &v); g->F64 = static_cast<double*>(v); }
+    ok = ok && alloc(8 * g->nT, &v); g->Tg = static_cast<double*>(v);
+  }
+  if (!ok) {
+    hotrg_group_destroy(g);
+    return HOTRG_ENOMEM;
+  }
+  *out = g;
+  return HOTRG_OK;
+}
+
+void hotrg_group_destroy(hotrg_group g) {
+  if (!g) return;
+  if (g->stream) cudaStreamSynchronize(g->stream);
+  else cudaDeviceSynchronize();
+  for (void* v : g->allocs) cudaFree(v);
+  delete g;
+}
+
+unsigned long long hotrg_group_launches(hotrg_group g) { return g ? g->grouped_launches : 0; }
+
+hotrg_status hotrg_forward_group_tensor(hotrg_group g, hotrg_plan* plans, int count,
+                                        const double* T0_host, double* lnz) {
+  hotrg_status r = group_check(g, plans, count);
+  if (r != HOTRG_OK) return r;
+  if (!T0_host) return HOTRG_EINVAL;
+  const long long n0 = (long long)plans[0]->cfg.d0 * plans[0]->cfg.d0 * plans[0]->cfg.d0 *
+                       plans[0]->cfg.d0;
+  for (long long i = 0; i < n0 * count; ++i)
+    if (!std::isfinite(T0_host[i])) return fail(plans[0], HOTRG_EINVAL, "T0 has a non-finite entry");
+  for (int i = 0; i < count; ++i)
+    CK2(plans[i], cudaMemcpyAsync(plans[i]->T[0], T0_host + i * n0, sizeof(double) * n0,
+                                  cudaMemcpyHostToDevice, g->stream));
+  r = group_run(g, plans, count);
+  if (r != HOTRG_OK) return r;
+  return group_outputs(plans, count, lnz);
+}
+
+hotrg_status hotrg_forward_group_ising(hotrg_group g, hotrg_plan* plans, int count,
+                                       const double* beta, const double* J, const double* h,
+                                       double* lnz) {
+  hotrg_status r = group_check(g, plans, count);
+  if (r != HOTRG_OK) return r;
+  if (!beta || !J || !h) return HOTRG_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (plans[i]->cfg.d0 != 2) return fail(plans[i], HOTRG_EINVAL, "Ising tensor needs d0 == 2");
+    if (!std::isfinite(beta[i]) || !std::isfinite(J[i]) || !std::isfinite(h[i]) ||
+        beta[i] * J[i] < 0)
+      return fail(plans[i], HOTRG_EINVAL, "Ising parameters must be finite with beta*J >= 0");
+  }
+  for (int i = 0; i < count; ++i)
+    CK2(plans[i], ising_t0(beta[i], J[i], h[i], plans[i]->T[0], plans[i]->dT0, g->stream));
+  r = group_run(g, plans, count);
+  if (r != HOTRG_OK) return r;
+  for (int i = 0; i < count; ++i) plans[i]->fwd_ising = true;
+  return group_outputs(plans, count, lnz);
 }
 
 hotrg_status hotrg_isometry_sides(hotrg_plan p, int* side) {

@@ -35,17 +35,44 @@ def grid_derivative(x: np.ndarray, y: np.ndarray) -> np.ndarray:
 def ising_thermodynamics(betas, d_cut: int, n_steps: int, precision: str = "fp64",
                          split_from_step: int = 1, J: float = 1.0, h: float = 0.0,
                          hi_precision_steps: int = 2, concurrent: int = 1,
-                         sm_reserve: int = 0) -> dict:
+                         sm_reserve: int = 0, grouped: int = 0) -> dict:
     """ln Z / N, f, u and c on a beta grid.  ``concurrent`` plans, each on its
     own CUDA stream and host thread, take the betas round-robin (so that one
     solve's latency-bound eigensolver kernels run beside another's
     contractions; ``sm_reserve`` SMs are left free by each plan's
-    contraction GEMMs for that); every beta's result is the same as with one
-    plan."""
+    contraction GEMMs for that).  ``grouped`` > 1 (split precision): the betas
+    go in batches of that many through one grouped forward each (every
+    contraction stage of the batch one tensor-core launch), then each plan's
+    backward.  Every beta's result is the same as with one plan."""
     import threading
     betas = np.asarray(betas, dtype=np.float64)
     lnz = np.empty_like(betas)
     dlnz = np.empty_like(betas)
+    if grouped > 1 and precision != "fp64":
+        import torch
+        from . import Group
+        G = min(int(grouped), len(betas))
+        st = torch.cuda.Stream()
+        kw = dict(split_from_step=split_from_step, want_grad=True,
+                  hi_precision_steps=hi_precision_steps)
+        plans = [Plan(2, d_cut, n_steps, precision, stream=st.cuda_stream, **kw)
+                 for _ in range(G)]
+        try:
+            with Group(2, d_cut, n_steps, precision, max_count=G, stream=st.cuda_stream,
+                       **kw) as grp:
+                for i0 in range(0, len(betas), G):
+                    bs = betas[i0:i0 + G]
+                    ps = plans[:len(bs)]
+                    lnz[i0:i0 + len(bs)] = grp.forward_ising(ps, bs, J, h)
+                    for j, p in enumerate(ps):
+                        _, dlnz[i0 + j] = p.backward(want_dbeta=True)
+        finally:
+            for p in plans:
+                p.close()
+        u = -dlnz
+        c = (-betas ** 2 * grid_derivative(betas, u) if len(betas) >= 3
+             else np.full_like(betas, np.nan))
+        return dict(beta=betas, lnz=lnz, f=-lnz / betas, u=u, c=c)
     C = max(1, min(int(concurrent), len(betas)))
     streams = []
     if C > 1:

@@ -65,3 +65,19 @@ def test_budget_admission_and_rejection():
     assert st["peak_bytes"] <= int(1.5 * b16)
     lnz = [r.lnz_per_site for r in res]
     assert max(lnz) - min(lnz) < 1e-13
+
+
+def test_same_shape_requests_run_as_a_grouped_forward():
+    """Forward-only split requests of one D_cut queued together run as one
+    grouped forward (their contractions one tensor-core launch per stage);
+    every result equals the request's own solve bit for bit."""
+    reqs = [(0.30 + 0.05 * i, 0.01 * i, 16, 12 + (i % 3), False, "bf16x6", 5) for i in range(6)]
+    ref = [alone(*m) for m in reqs]
+    with hot.Server(hbm_budget_bytes=40 << 30, max_slots=1) as srv:
+        tickets = [srv.submit(b, 1.0, h, d, n, g, pr, sf) for (b, h, d, n, g, pr, sf) in reqs]
+        res = [srv.wait(t) for t in tickets]
+        st = srv.stats()
+    assert st["failed"] == 0 and st["grouped"] >= 2 and st["groups"] >= 1
+    for (lnz, _), r in zip(ref, res):
+        assert r.status == 0
+        assert r.lnz_per_site == lnz

@@ -102,3 +102,15 @@ def test_ising_grid_concurrent_plans_equal_single_plan():
     b = ising_thermodynamics(betas, 16, 16, "bf16x6", split_from_step=5, concurrent=3,
                              sm_reserve=16)
     assert np.array_equal(a["lnz"], b["lnz"]) and np.array_equal(a["u"], b["u"])
+
+
+@pytest.mark.gpu
+def test_ising_grid_grouped_forwards_equal_single_plan():
+    """The grid in grouped forwards (each stage of a batch of betas one
+    tensor-core launch, then each plan's backward) gives every beta the same
+    result as one plan, bit for bit, including a last, partial batch."""
+    from paper_1912_02780_gb300.observables import ising_thermodynamics
+    betas = np.linspace(0.40, 0.46, 7)
+    a = ising_thermodynamics(betas, 16, 16, "bf16x6", split_from_step=5)
+    b = ising_thermodynamics(betas, 16, 16, "bf16x6", split_from_step=5, grouped=3)
+    assert np.array_equal(a["lnz"], b["lnz"]) and np.array_equal(a["u"], b["u"])
