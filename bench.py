@@ -610,8 +610,10 @@ def run_group(args):
     """Grouped forward against the same solves one after another and on
     concurrent streams: G Ising solves (beta spread over [0.30, 0.60], h = 0)
     of one shape per D_cut, BF16X6 split from step 5, forward only, subspace
-    eigensolver; solves/s of each form and the launch counts; every grouped
-    result compared with the solo one (bit for bit)."""
+    eigensolver; the grouped forward with all plans on one stream and with
+    each plan on its own stream (overlapping eigensolves); solves/s of each
+    form and the launch counts; every result compared with the solo one (bit
+    for bit)."""
     import torch
     import paper_1912_02780_gb300 as hot
     G, n = args.group_size, 30
@@ -634,12 +636,16 @@ def run_group(args):
         def grouped():
             return list(grp.forward_ising(plans, betas))
 
+        def grouped_streams():
+            return list(grp.forward_ising(cplans, betas))
+
         def concurrent():
             return list(pool.map(lambda i: cplans[i].forward_ising(betas[i])[0], range(G)))
 
         out = {"d_cut": D, "solves": G}
         ref = None
-        for name, fn in (("solo", solo), ("grouped", grouped), ("concurrent", concurrent)):
+        for name, fn in (("solo", solo), ("grouped", grouped), ("concurrent", concurrent),
+                         ("grouped_streams", grouped_streams)):
             for _ in range(args.warmup):
                 r = fn()
             torch.cuda.synchronize()

@@ -293,12 +293,15 @@ hotrg_status hotrg_forward_xy(hotrg_plan plan, double tau, double J, double* lnz
  * different requests).  A group holds the batched operand buffers of one
  * problem shape for up to max_count plans; hotrg_forward_group_* runs the
  * forwards of `count` plans created with that config (any depths set with
- * hotrg_plan_set_steps) in lockstep on the group's stream, which every plan
- * must be bound to: per step each plan forms its own isometry (Gram matrix and
- * eigensolve), then on split steps whose free leg fits one chunk the three
- * contractions of all plans are ONE tensor-core launch per stage (each
- * problem's operand rows at its own offset of the group's buffers), then each
- * plan normalises; other steps run plan by plan.  Every plan ends as after its
+ * hotrg_plan_set_steps) in lockstep: one host thread per plan issues the
+ * plan's work on the plan's own stream (plans on different streams overlap
+ * their eigensolves); per step each plan forms its own isometry (Gram matrix
+ * and eigensolve) and, on split steps whose free leg fits one chunk, prepares
+ * its operands in the group's buffers; the three contractions of all plans are
+ * then ONE tensor-core launch per stage on the group's stream (each problem's
+ * operand rows at its own offset of the group's buffers, ordered after every
+ * plan's preparation by events), after which each plan normalises on its own
+ * stream; other steps run plan by plan.  The call synchronises all streams.  Every plan ends as after its
  * own forward (results bit-identical; hotrg_backward, diagnostics and the
  * outputs work per plan).  T0_host: count * d0^4 float64 (plan i's tensor at
  * i * d0^4); beta, J, h: count values; lnz (host, may be NULL): count values.

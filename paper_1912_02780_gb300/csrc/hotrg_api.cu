@@ -22,6 +22,9 @@
 #include <cusolverDn.h>
 #include <algorithm>
 #include <atomic>
+#include <condition_variable>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -1338,6 +1341,8 @@ struct hotrg_group_s {
   double* F64 = nullptr;
   double* Tg = nullptr;
   unsigned long long grouped_launches = 0;
+  std::vector<cudaEvent_t> ev;     // per plan slot: its operands are prepared
+  cudaEvent_t ev_done = nullptr;   // the grouped contractions of a step are issued
 };
 
 namespace {
@@ -1347,27 +1352,37 @@ TcOperand gopnd(const __nv_bfloat16* ptr, int count, int pitch_rows, int K, int 
   return opnd(ptr, count * pitch_rows, K, np, stride);
 }
 
-// The three contractions of step k of every plan in `ps` as one grouped launch
-// per stage (mirrors contract_split for a single chunk).
-hotrg_status contract_split_group(hotrg_group g, hotrg_plan* ps, int cnt, int k) {
+// Operand preparation of plan q for its place `slot` of a grouped step k, on
+// the plan's own stream: the four bf16-split operands of the three stages,
+// written into the group's batched buffers.
+hotrg_status group_prep(hotrg_group g, hotrg_plan q, int slot, int k) {
+  hotrg_plan p = q;   // the plan errors are reported on
+  const StepGeom& s = q->L.g[k - 1];
+  const int X = s.X, Y = s.Y, Xp = s.Xp, np = s.np;
+  const long long N = s.N, Y2 = (long long)Y * Y, XY2 = (long long)X * Y * Y;
+  const GroupGeom gg = group_geom(s);
+  Stage sc(q, kStPrep);
+  const double* Ek = E_of(q, k);
+  const double* T = q->T[k - 1];
+  CK(gsplit(q, Ek, map2(X, 1, N), map_lin(X), Xp * X, X, np, g->sW1, g->W1 + slot * gg.pW1));
+  CK(gsplit(q, T, map3(Y, X, 1, Y2, Y), map_lin(XY2), Y * X * Y, X, np, g->sT1,
+            g->T1 + slot * gg.pT1));
+  CK(gsplit(q, T, map2(X, Y2, 1), map2(Y, Y, XY2), Y * X, X * Y, np, g->sP, g->P + slot * gg.pP));
+  CK(gsplit(q, Ek, map_lin(N), map_lin(1), Xp, X * X, np, g->sW3, g->W3 + slot * gg.pW3));
+  return HOTRG_OK;
+}
+
+// The three contractions of step k of every plan in `ps` (prepared by
+// group_prep) as one grouped launch per stage on the group's stream (mirrors
+// contract_split for a single chunk), then each plan's new tensor copied home.
+hotrg_status group_gemms(hotrg_group g, hotrg_plan* ps, int cnt, int k) {
   hotrg_plan p = ps[0];
   const StepGeom& s = p->L.g[k - 1];
   const int X = s.X, Y = s.Y, Xp = s.Xp, np = s.np;
-  const long long N = s.N, XY = (long long)X * Y, Y2 = (long long)Y * Y, XY2 = XY * Y;
+  const long long XY = (long long)X * Y;
   const long long Xp2 = (long long)Xp * Xp, X2 = (long long)X * X;
   cudaStream_t st = g->stream;
   const GroupGeom gg = group_geom(s);
-  for (int i = 0; i < cnt; ++i) {
-    hotrg_plan q = ps[i];
-    Stage sc(q, kStPrep);
-    const double* Ek = E_of(q, k);
-    const double* T = q->T[k - 1];
-    CK(gsplit(q, Ek, map2(X, 1, N), map_lin(X), Xp * X, X, np, g->sW1, g->W1 + i * gg.pW1));
-    CK(gsplit(q, T, map3(Y, X, 1, Y2, Y), map_lin(XY2), Y * X * Y, X, np, g->sT1,
-              g->T1 + i * gg.pT1));
-    CK(gsplit(q, T, map2(X, Y2, 1), map2(Y, Y, XY2), Y * X, X * Y, np, g->sP, g->P + i * gg.pP));
-    CK(gsplit(q, Ek, map_lin(N), map_lin(1), Xp, X * X, np, g->sW3, g->W3 + i * gg.pW3));
-  }
   const bool fuse = np == 3 && p->cfg.epilogue_split != 0;
   int p1r = 0, p1h = 0, p2r = 0, p2h = 0;
   const bool fuse1 = fuse && (Xp * X) % 128 == 0 && (XY % 128) == 0 && X % 2 == 0 &&
@@ -1383,77 +1398,81 @@ hotrg_status contract_split_group(hotrg_group g, hotrg_plan* ps, int cnt, int k)
     t.c_batch = c_batch;
     t.c_lim = c_lim;
   };
+  auto split_staged = [&](long long per, int rows, int K, long long plane, __nv_bfloat16* dst)
+      -> cudaError_t {
+    for (int i = 0; i < cnt; ++i) {
+      const long long off = i * per;
+      cudaError_t e = np == 4
+          ? grid_split(g->F64 + off, g->nF - off, map_lin(K), map_lin(1), rows, K, np, plane,
+                       dst + off, p->err, st, p->sms)
+          : grid_split(g->F32 + off, g->nF - off, map_lin(K), map_lin(1), rows, K, np, plane,
+                       dst + off, p->err, st, p->sms);
+      if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+  };
   // S1: U[(y x1' a)][(x2 j)] of every plan
-  {
-    Stage sc(p, kStS1);
-    TcGemm g1 = tcg(p, np, Xp * X, Y * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
-                    fuse1 ? kOutGridSplit : stage_mode(np), fuse1 ? (void*)g->U : staged(np),
-                    fuse1 ? g->sU : 0);
-    g1.m_fast = 1;
-    g1.seg_prow = p1r;
-    g1.seg_phalf = p1h;
-    batch(g1, gg.aW1, Y * X * Y, gg.pU, fuse1 ? g->sU : g->nF);
-    CK(tc_gemm(gopnd(g->W1, cnt, gg.aW1, X, np, g->sW1), gopnd(g->T1, cnt, Y * X * Y, X, np, g->sT1),
-               g1, st, p->tc_sms));
-    ++g->grouped_launches;
-    if (!fuse1)
-      for (int i = 0; i < cnt; ++i) {
-        const long long off = i * gg.pU;
-        if (np == 4)
-          CK(grid_split(g->F64 + off, g->nF - off, map_lin(XY), map_lin(1), Y * X * Xp, X * Y,
-                        np, g->sU, g->U + off, p->err, st, p->sms));
-        else
-          CK(grid_split(g->F32 + off, g->nF - off, map_lin(XY), map_lin(1), Y * X * Xp, X * Y,
-                        np, g->sU, g->U + off, p->err, st, p->sms));
-      }
-  }
+  TcGemm g1 = tcg(p, np, Xp * X, Y * X * Y, X, map2(X, Y, XY), map3(Y, X, 1, Xp * XY, X * Xp * XY),
+                  fuse1 ? kOutGridSplit : stage_mode(np), fuse1 ? (void*)g->U : staged(np),
+                  fuse1 ? g->sU : 0);
+  g1.m_fast = 1;
+  g1.seg_prow = p1r;
+  g1.seg_phalf = p1h;
+  batch(g1, gg.aW1, Y * X * Y, gg.pU, fuse1 ? g->sU : g->nF);
+  CK(tc_gemm(gopnd(g->W1, cnt, gg.aW1, X, np, g->sW1), gopnd(g->T1, cnt, Y * X * Y, X, np, g->sT1),
+             g1, st, p->tc_sms));
+  ++g->grouped_launches;
+  if (!fuse1) CK(split_staged(gg.pU, Y * X * Xp, X * Y, g->sU, g->U));
   // S2: V[(y a y')][(x1' x2')] of every plan
-  {
-    Stage sc(p, np == 4 ? kStS2Hi : kStS2);
-    TcGemm g2 = tcg(p, np, Y * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
-                    map2(X, 1, X2), fuse2 ? kOutGridSplit : stage_mode(np),
-                    fuse2 ? (void*)g->V : staged(np), fuse2 ? g->sV : 0);
-    g2.seg_prow = p2r;
-    g2.seg_phalf = p2h;
-    g2.n_group = stage2_group(p->cfg);
-    batch(g2, gg.aU, Y * X, gg.pV, fuse2 ? g->sV : g->nF);
-    CK(tc_gemm(gopnd(g->U, cnt, gg.aU, X * Y, np, g->sU), gopnd(g->P, cnt, Y * X, X * Y, np, g->sP),
-               g2, st, p->tc_sms));
-    ++g->grouped_launches;
-    if (!fuse2)
-      for (int i = 0; i < cnt; ++i) {
-        const long long off = i * gg.pV;
-        if (np == 4)
-          CK(grid_split(g->F64 + off, g->nF - off, map_lin(X2), map_lin(1), Y * Xp * Y, X * X,
-                        np, g->sV, g->V + off, p->err, st, p->sms));
-        else
-          CK(grid_split(g->F32 + off, g->nF - off, map_lin(X2), map_lin(1), Y * Xp * Y, X * X,
-                        np, g->sV, g->V + off, p->err, st, p->sms));
-      }
-  }
+  TcGemm g2 = tcg(p, np, Y * X * Xp, Y * X, X * Y, map3(Xp, X, Y * X2, X, Xp * Y * X2),
+                  map2(X, 1, X2), fuse2 ? kOutGridSplit : stage_mode(np),
+                  fuse2 ? (void*)g->V : staged(np), fuse2 ? g->sV : 0);
+  g2.seg_prow = p2r;
+  g2.seg_phalf = p2h;
+  g2.n_group = stage2_group(p->cfg);
+  batch(g2, gg.aU, Y * X, gg.pV, fuse2 ? g->sV : g->nF);
+  CK(tc_gemm(gopnd(g->U, cnt, gg.aU, X * Y, np, g->sU), gopnd(g->P, cnt, Y * X, X * Y, np, g->sP),
+             g2, st, p->tc_sms));
+  ++g->grouped_launches;
+  if (!fuse2) CK(split_staged(gg.pV, Y * Xp * Y, X * X, g->sV, g->V));
   // S3: T'[y][y'][a][b] of every plan into the group's buffer, then home
-  {
-    Stage sc(p, kStS3);
-    TcGemm g3 = tcg(p, np, Y * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1),
-                    kOutF64, g->Tg, 0);
-    batch(g3, gg.aV, Xp, gg.pT, g->nT);
-    CK(tc_gemm(gopnd(g->V, cnt, gg.aV, X * X, np, g->sV), gopnd(g->W3, cnt, Xp, X * X, np, g->sW3),
-               g3, st, p->tc_sms));
-    ++g->grouped_launches;
-    for (int i = 0; i < cnt; ++i)
-      CK(cudaMemcpyAsync(ps[i]->T[k], g->Tg + i * gg.pT, sizeof(double) * gg.pT,
-                         cudaMemcpyDeviceToDevice, st));
-  }
+  TcGemm g3 = tcg(p, np, Y * Xp * Y, Xp, X * X, map3(Y, Xp, Xp2, Xp, Y * Xp2), map_lin(1), kOutF64,
+                  g->Tg, 0);
+  batch(g3, gg.aV, Xp, gg.pT, g->nT);
+  CK(tc_gemm(gopnd(g->V, cnt, gg.aV, X * X, np, g->sV), gopnd(g->W3, cnt, Xp, X * X, np, g->sW3),
+             g3, st, p->tc_sms));
+  ++g->grouped_launches;
+  for (int i = 0; i < cnt; ++i)
+    CK(cudaMemcpyAsync(ps[i]->T[k], g->Tg + i * gg.pT, sizeof(double) * gg.pT,
+                       cudaMemcpyDeviceToDevice, st));
   return HOTRG_OK;
 }
+
+// A reusable barrier for the group's host threads.
+struct Barrier {
+  std::mutex m;
+  std::condition_variable cv;
+  int n, count = 0;
+  unsigned gen = 0;
+  explicit Barrier(int n_) : n(n_) {}
+  void wait() {
+    std::unique_lock<std::mutex> l(m);
+    const unsigned my = gen;
+    if (++count == n) {
+      count = 0;
+      ++gen;
+      cv.notify_all();
+    } else {
+      cv.wait(l, [&] { return gen != my; });
+    }
+  }
+};
 
 hotrg_status group_check(hotrg_group g, hotrg_plan* ps, int cnt) {
   if (!g || !ps || cnt < 1 || cnt > g->max_count) return HOTRG_EINVAL;
   for (int i = 0; i < cnt; ++i) {
     hotrg_plan q = ps[i];
     if (!q) return HOTRG_EINVAL;
-    if (q->stream != g->stream)
-      return fail(q, HOTRG_EINVAL, "grouped forward: every plan must be on the group's stream");
     if (q->cfg.scheme != 0 || q->cfg.w_given || q->cfg.w_rule != 0 ||
         q->L.g.size() != g->L.g.size() || q->cfg.epilogue_split != ps[0]->cfg.epilogue_split ||
         q->cfg.stage2_n_group != ps[0]->cfg.stage2_n_group ||
@@ -1471,7 +1490,13 @@ hotrg_status group_check(hotrg_group g, hotrg_plan* ps, int cnt) {
   return HOTRG_OK;
 }
 
-// Lockstep forward of the plans (T0 already in each plan's T[0]).
+// Lockstep forward of the plans (T0 already in each plan's T[0]).  One host
+// thread per plan issues its work on the plan's own stream, so the plans'
+// eigensolves (and their guards' host reads) overlap; per grouped step the
+// threads meet twice: after each has formed its isometry and prepared its
+// operands (an event on its stream), the first thread issues the grouped
+// contractions on the group's stream after all those events; after them (one
+// event) each plan normalises on its own stream.
 hotrg_status group_run(hotrg_group g, hotrg_plan* ps, int cnt) {
   int kmax = 0;
   for (int i = 0; i < cnt; ++i) {
@@ -1482,35 +1507,87 @@ hotrg_status group_run(hotrg_group g, hotrg_plan* ps, int cnt) {
     if (r != HOTRG_OK) return r;
     kmax = std::max(kmax, q->n_run);
   }
-  std::vector<hotrg_plan> act;
-  for (int k = 1; k <= kmax; ++k) {
+  // the grouped work of step k must follow the copy-in and set-up above on
+  // every plan's stream
+  std::vector<hotrg_status> st(cnt, HOTRG_OK);
+  hotrg_status lead = HOTRG_OK;
+  std::atomic<bool> failed{false};
+  Barrier bar(cnt);
+  auto active_of = [&](int k, std::vector<int>& act) {
     act.clear();
     for (int i = 0; i < cnt; ++i)
-      if (ps[i]->n_run >= k) act.push_back(ps[i]);
-    for (hotrg_plan q : act) {
-      hotrg_status r = step_eigh(q, k);
-      if (r != HOTRG_OK) return r;
-    }
-    if (act.size() > 1 && groupable(g->L.g[k - 1])) {
-      hotrg_status r = contract_split_group(g, act.data(), (int)act.size(), k);
-      if (r != HOTRG_OK) return r;
-    } else {
-      for (hotrg_plan q : act) {
-        hotrg_status r = step_contract(q, k);
-        if (r != HOTRG_OK) return r;
+      if (ps[i]->n_run >= k) act.push_back(i);
+  };
+  auto body = [&](int i) {
+    hotrg_plan q = ps[i];
+    std::vector<int> act;
+    for (int k = 1; k <= kmax; ++k) {
+      active_of(k, act);
+      const bool grouped = act.size() > 1 && groupable(g->L.g[k - 1]);
+      const bool mine = q->n_run >= k;
+      if (mine && !failed.load()) {
+        hotrg_status r = step_eigh(q, k);
+        if (r == HOTRG_OK && grouped) {
+          const int slot = (int)(std::find(act.begin(), act.end(), i) - act.begin());
+          r = group_prep(g, q, slot, k);
+          if (r == HOTRG_OK && cudaEventRecord(g->ev[i], q->stream) != cudaSuccess)
+            r = fail(q, HOTRG_ECUDA, "cudaEventRecord failed");
+        }
+        if (r == HOTRG_OK && !grouped) r = step_contract(q, k);
+        if (r != HOTRG_OK) {
+          st[i] = r;
+          failed = true;
+        }
+      }
+      if (grouped) {
+        bar.wait();
+        if (i == 0 && !failed.load()) {
+          hotrg_status r = HOTRG_OK;
+          for (int j : act)
+            if (cudaStreamWaitEvent(g->stream, g->ev[j], 0) != cudaSuccess)
+              r = fail(ps[0], HOTRG_ECUDA, "cudaStreamWaitEvent failed");
+          std::vector<hotrg_plan> ap;
+          for (int j : act) ap.push_back(ps[j]);
+          if (r == HOTRG_OK) r = group_gemms(g, ap.data(), (int)ap.size(), k);
+          if (r == HOTRG_OK && cudaEventRecord(g->ev_done, g->stream) != cudaSuccess)
+            r = fail(ps[0], HOTRG_ECUDA, "cudaEventRecord failed");
+          if (r != HOTRG_OK) {
+            lead = r;
+            failed = true;
+          }
+        }
+        bar.wait();
+        if (mine && !failed.load() && cudaStreamWaitEvent(q->stream, g->ev_done, 0) != cudaSuccess) {
+          st[i] = fail(q, HOTRG_ECUDA, "cudaStreamWaitEvent failed");
+          failed = true;
+        }
+      }
+      if (mine && !failed.load()) {
+        hotrg_status r = step_finish(q, k);
+        if (r != HOTRG_OK) {
+          st[i] = r;
+          failed = true;
+        }
       }
     }
-    for (hotrg_plan q : act) {
-      hotrg_status r = step_finish(q, k);
-      if (r != HOTRG_OK) return r;
+    if (!failed.load()) {
+      hotrg_status r = forward_end(q);
+      if (r != HOTRG_OK) {
+        st[i] = r;
+        failed = true;
+      }
     }
-  }
-  for (int i = 0; i < cnt; ++i) {
-    hotrg_status r = forward_end(ps[i]);
-    if (r != HOTRG_OK) return r;
-  }
+  };
+  std::vector<std::thread> th;
+  for (int i = 1; i < cnt; ++i) th.emplace_back(body, i);
+  body(0);
+  for (auto& t : th) t.join();
+  if (lead != HOTRG_OK) return lead;
+  for (int i = 0; i < cnt; ++i)
+    if (st[i] != HOTRG_OK) return st[i];
   // grouped launches report device errors in the first plan's error word
   CK2(ps[0], cudaStreamSynchronize(g->stream));
+  for (int i = 0; i < cnt; ++i) CK2(ps[i], cudaStreamSynchronize(ps[i]->stream));
   int w0[2] = {0, 0};
   CK2(ps[0], cudaMemcpy(w0, ps[0]->err, 2 * sizeof(int), cudaMemcpyDeviceToHost));
   for (int i = 0; i < cnt; ++i) {
@@ -2210,6 +2287,13 @@ hotrg_status hotrg_group_create(const hotrg_config* cfg, int max_count, void* cu
     hotrg_group_destroy(g);
     return HOTRG_ENOMEM;
   }
+  g->ev.assign(max_count, nullptr);
+  for (int i = 0; i < max_count; ++i)
+    if (cudaEventCreateWithFlags(&g->ev[i], cudaEventDisableTiming) != cudaSuccess) ok = false;
+  if (!ok || cudaEventCreateWithFlags(&g->ev_done, cudaEventDisableTiming) != cudaSuccess) {
+    hotrg_group_destroy(g);
+    return HOTRG_ECUDA;
+  }
   *out = g;
   return HOTRG_OK;
 }
@@ -2218,6 +2302,9 @@ void hotrg_group_destroy(hotrg_group g) {
   if (!g) return;
   if (g->stream) cudaStreamSynchronize(g->stream);
   else cudaDeviceSynchronize();
+  for (cudaEvent_t e : g->ev)
+    if (e) cudaEventDestroy(e);
+  if (g->ev_done) cudaEventDestroy(g->ev_done);
   for (void* v : g->allocs) cudaFree(v);
   delete g;
 }
@@ -2235,7 +2322,7 @@ hotrg_status hotrg_forward_group_tensor(hotrg_group g, hotrg_plan* plans, int co
     if (!std::isfinite(T0_host[i])) return fail(plans[0], HOTRG_EINVAL, "T0 has a non-finite entry");
   for (int i = 0; i < count; ++i)
     CK2(plans[i], cudaMemcpyAsync(plans[i]->T[0], T0_host + i * n0, sizeof(double) * n0,
-                                  cudaMemcpyHostToDevice, g->stream));
+                                  cudaMemcpyHostToDevice, plans[i]->stream));
   r = group_run(g, plans, count);
   if (r != HOTRG_OK) return r;
   return group_outputs(plans, count, lnz);
@@ -2254,7 +2341,7 @@ hotrg_status hotrg_forward_group_ising(hotrg_group g, hotrg_plan* plans, int cou
       return fail(plans[i], HOTRG_EINVAL, "Ising parameters must be finite with beta*J >= 0");
   }
   for (int i = 0; i < count; ++i)
-    CK2(plans[i], ising_t0(beta[i], J[i], h[i], plans[i]->T[0], plans[i]->dT0, g->stream));
+    CK2(plans[i], ising_t0(beta[i], J[i], h[i], plans[i]->T[0], plans[i]->dT0, plans[i]->stream));
   r = group_run(g, plans, count);
   if (r != HOTRG_OK) return r;
   for (int i = 0; i < count; ++i) plans[i]->fwd_ising = true;

@@ -81,6 +81,8 @@ struct hotrg_server_s {
   std::list<PooledPlan> pool;   // built plans of all slots, front = most recently used
   std::vector<cudaStream_t> streams;   // one per slot; owned by the server, destroyed after
                                        // every pooled plan (plans keep a stream handle)
+  std::vector<std::vector<cudaStream_t>> gstreams;   // per slot: the streams of a grouped
+                                                     // forward's plans
   int slots = 0;
   std::vector<int> busy;
   size_t bytes_in_use = 0, peak_bytes = 0;
@@ -309,8 +311,12 @@ void worker(hotrg_server_s* s, int slot) {
       s->groups_run += 1;
     }
     lk.unlock();
-    for (int i : ok) {
-      sts[i] = hotrg_plan_set_stream(plans[i], stream);
+    const bool grouped_run = group && ok.size() > 1;
+    for (size_t q = 0; q < ok.size(); ++q) {
+      const int i = ok[q];
+      // a grouped forward's plans run on streams of their own (their eigensolves
+      // overlap); the grouped contractions run on the slot's stream
+      sts[i] = hotrg_plan_set_stream(plans[i], grouped_run ? s->gstreams[slot][q] : stream);
       if (sts[i] == HOTRG_OK) sts[i] = hotrg_plan_set_steps(plans[i], jobs[i].req.n_steps);
     }
     std::vector<hotrg_result> res(jobs.size());
@@ -367,6 +373,7 @@ void worker(hotrg_server_s* s, int slot) {
   }
   lk.unlock();
   cudaStreamSynchronize(stream);
+  for (cudaStream_t g : s->gstreams[slot]) cudaStreamSynchronize(g);
 }
 
 }  // namespace
@@ -387,13 +394,22 @@ hotrg_status hotrg_server_create(size_t hbm_budget_bytes, int max_slots, hotrg_s
   s->busy.assign(max_slots, 0);
   s->groups.assign(max_slots, {});
   s->streams.assign(max_slots, nullptr);
-  for (int i = 0; i < max_slots; ++i) {
-    if (cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) != cudaSuccess) {
-      cudaGetLastError();
-      for (int j = 0; j < i; ++j) cudaStreamDestroy(s->streams[j]);
-      delete s;
-      return HOTRG_ECUDA;
+  s->gstreams.assign(max_slots, std::vector<cudaStream_t>(kGroupMax, nullptr));
+  bool ok = true;
+  for (int i = 0; i < max_slots && ok; ++i) {
+    ok = cudaStreamCreateWithFlags(&s->streams[i], cudaStreamNonBlocking) == cudaSuccess;
+    for (int j = 0; j < kGroupMax && ok; ++j)
+      ok = cudaStreamCreateWithFlags(&s->gstreams[i][j], cudaStreamNonBlocking) == cudaSuccess;
+  }
+  if (!ok) {
+    cudaGetLastError();
+    for (int i = 0; i < max_slots; ++i) {
+      if (s->streams[i]) cudaStreamDestroy(s->streams[i]);
+      for (cudaStream_t g : s->gstreams[i])
+        if (g) cudaStreamDestroy(g);
     }
+    delete s;
+    return HOTRG_ECUDA;
   }
   for (int i = 0; i < max_slots; ++i) s->workers.emplace_back(worker, s, i);
   *out = s;
@@ -475,6 +491,9 @@ void hotrg_server_destroy(hotrg_server s) {
   s->groups.clear();
   for (cudaStream_t st : s->streams)
     if (st) cudaStreamDestroy(st);
+  for (auto& v : s->gstreams)
+    for (cudaStream_t st : v)
+      if (st) cudaStreamDestroy(st);
   delete s;
 }
 
