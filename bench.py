@@ -656,12 +656,12 @@ def run_group(args):
             torch.cuda.synchronize()
             dt = (time.perf_counter() - t0) / args.steps
             out[name] = {"solves_per_s": G / dt, "ms": 1e3 * dt,
-                         "launches_per_round": (hot.kernel_launches() - l0) // args.steps}
+                         "launches_per_iteration": (hot.kernel_launches() - l0) // args.steps}
             if ref is None:
                 ref = r
             else:
                 out[name]["bit_identical_to_solo"] = bool(list(r) == list(ref))
-        out["grouped_launches_per_round"] = grp.launches()
+        out["grouped_launches_total"] = grp.launches()
         rows.append(out)
         print(json.dumps(out), flush=True)
         pool.shutdown()
