@@ -96,3 +96,52 @@ def test_dtrg_driver_needs_one_input():
         dtrg_sweeps(2, 6, 4, n_sweeps=1)                                  # neither T0 nor beta
     with pytest.raises(ValueError):
         dtrg_sweeps(2, 6, 4, n_sweeps=1, T0=np.ones((2, 2, 2, 2)), beta=0.4)   # both
+
+
+def test_scheme_w_rule_and_group_host_checks(hot):
+    """Host-side validation and sizing of the scheme-(b), w_rule and grouped
+    forward options (no GPU needed)."""
+    L = hot.lib()
+    out = ctypes.c_size_t(0)
+    bad = [dict(scheme=2), dict(scheme=-1), dict(w_rule=2),
+           dict(w_rule=1, want_grad=True, fixed_w_grad=True, w_given=True)]
+    for kw in bad:
+        c = hot.make_config(4, 16, 8, **kw)
+        assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1, kw
+    c = hot.make_config(4, 16, 8, scheme=1)
+    c.chain_steps = 2                      # the binding passes 0 / 1; the library checks
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
+    c = hot.make_config(4, 5000, 8, scheme=1)
+    assert L.hotrg_plan_workspace_bytes(ctypes.byref(c), ctypes.byref(out)) == 1
+    # scheme (b) keeps the vertical legs at d0: much smaller than scheme (a) at the same D_cut
+    a = hot.workspace_bytes(4, 64, 12, want_grad=False)
+    b = hot.workspace_bytes(4, 64, 12, want_grad=False, scheme=1)
+    assert 0 < b < a
+    # w_rule 1 adds the right side's eigenvectors
+    assert hot.workspace_bytes(4, 16, 8, w_rule=1) > hot.workspace_bytes(4, 16, 8)
+    # grouped-forward buffers: none without split steps, growing with the group size
+    def gbytes(cfg, count):
+        n = ctypes.c_size_t(0)
+        assert L.hotrg_group_workspace_bytes(ctypes.byref(cfg), count, ctypes.byref(n)) == 0
+        return n.value
+    assert gbytes(hot.make_config(2, 16, 20), 4) == 0
+    cs = hot.make_config(2, 16, 20, precision="bf16x6", split_from_step=5)
+    assert 0 < gbytes(cs, 2) < gbytes(cs, 4)
+    n = ctypes.c_size_t(0)
+    assert L.hotrg_group_workspace_bytes(ctypes.byref(cs), 0, ctypes.byref(n)) == 1
+    assert L.hotrg_group_workspace_bytes(ctypes.byref(cs), 65, ctypes.byref(n)) == 1
+
+
+def test_xy_per_site_conversion_matches_oracle():
+    """The scheme-(b) driver's conversion of ln Z per copy of T0 to per-site
+    thermodynamics agrees with the oracle's."""
+    from oracle import xtrg
+    from paper_1912_02780_gb300 import xtrg as gx
+    out = np.array([0.7, 0.35, 0.18])
+    depths = np.array([1, 2, 3])
+    tau = 0.01
+    beta, lnz_site, f = gx.per_site(out, depths, tau)
+    for k, o, b, l, ff in zip(depths, out, beta, lnz_site, f):
+        assert b == tau * 2.0 ** (k + 1)
+        assert abs(l - xtrg.lnz_per_site(o, k + 1)) < 1e-15
+        assert abs(ff + l / b) < 1e-15
