@@ -92,8 +92,10 @@ typedef struct {
                                power iteration on eigh_block vectors with FP64 Householder QR,
                                then FP64 Rayleigh-Ritz; the products G Q run on the
                                four-plane tensor-core GEMM on split steps, in FP64
-                               otherwise; used where 4 D' < X^2).  Plans with gradients
-                               always take all eigenpairs.                                */
+                               otherwise; used where 4 D' < X^2).  Plans with full
+                               gradients always take all eigenpairs; fixed_w_grad plans
+                               (whose backward needs only the kept ones) and forward-only
+                               plans follow eigh_mode.  w_rule 1 ignores it.              */
   int eigh_power_iters;     /* power iterations of eigh_mode 1 (<= 0: 4)                   */
   int eigh_block;           /* vectors in the block of eigh_mode 1 (<= 0: 4 D'; at least
                                D' + 1)                                                     */
