@@ -1578,8 +1578,18 @@ hotrg_status group_run(hotrg_group g, hotrg_plan* ps, int cnt) {
       }
     }
   };
+  // the plans live on the caller's current device; the helper threads use it too
+  int dev = 0;
+  CK2(ps[0], cudaGetDevice(&dev));
   std::vector<std::thread> th;
-  for (int i = 1; i < cnt; ++i) th.emplace_back(body, i);
+  for (int i = 1; i < cnt; ++i)
+    th.emplace_back([&, i] {
+      if (cudaSetDevice(dev) != cudaSuccess) {
+        st[i] = HOTRG_ECUDA;
+        failed = true;
+      }
+      body(i);
+    });
   body(0);
   for (auto& t : th) t.join();
   if (lead != HOTRG_OK) return lead;
