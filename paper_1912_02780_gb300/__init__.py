@@ -441,8 +441,9 @@ class Plan:
 class Group:
     """Grouped forward of several plans of one shape (see include/hotrg.h:
     hotrg_group_*): the same keyword arguments as ``Plan`` describe the
-    shape; every plan passed to it must be created with them and bound to the
-    same stream."""
+    shape, and every plan passed to it must be created with them.  Each plan
+    runs on its own stream (plans on different streams overlap their
+    eigensolves); the grouped contractions run on the group's ``stream``."""
 
     def __init__(self, d0: int, d_cut: int, n_steps: int, precision="fp64", max_count: int = 8,
                  stream: Optional[int] = None, **kw):
