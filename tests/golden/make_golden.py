@@ -18,6 +18,7 @@ Cases:
   c2_grid     Ising, 64 betas on [0.30, 0.60], D_cut = 32, 30 steps (forward + d/dbeta)
   c4_d96_s0_n7  random T0 (d0 = 4, seed 0), D_cut = 96, 7 steps (forward; steps 5-7 at the
               full D_cut = 96 bond dimensions)
+  c4_d96_s0   the same tensor, D_cut = 96, 30 steps (forward; hours on the CPU)
 """
 import json
 import os
@@ -71,6 +72,9 @@ def main(cases):
             seed = int(c[len("c4_d64_s"):])
             fwd_case(c, synth.random_symmetric_T0(seed, 4), 64, 30,
                      dict(model="random reflection-symmetric T0", d0=4, seed=seed))
+        elif c == "c4_d96_s0":
+            fwd_case(c, synth.random_symmetric_T0(0, 4), 96, 30,
+                     dict(model="random reflection-symmetric T0", d0=4, seed=0))
         elif c == "c4_d96_s0_n7":
             fwd_case(c, synth.random_symmetric_T0(0, 4), 96, 7,
                      dict(model="random reflection-symmetric T0", d0=4, seed=0))
